@@ -1,0 +1,31 @@
+"""Plain FP64 CPU oracle for the hybrid nodal-staggered PSATD PIC step.
+
+TEST INFRASTRUCTURE ONLY.  This package is a slow, direct restatement of the
+method of Zoni et al., "A Hybrid Nodal-Staggered Pseudo-Spectral
+Electromagnetic Particle-In-Cell Method with Finite-Order Centering"
+(arXiv 2106.12919), written to check the CUDA path.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import it.  The product path never does, and the oracle never
+imports the product package: the two share no code.
+
+Every function follows the paper's notation and cites the section / equation it
+restates.  Loops are vectorised over particles or grid points only; there is no
+blocking, fusion or reordering beyond what the cited definitions state.
+
+Modules
+-------
+fornberg     Fornberg coefficients, modified wave numbers, centering symbol
+             (Sec. 3, Sec. 4.1, App. C).
+grid         Yee staggering, discrete Fourier conventions (App. A.1) and the
+             finite-order centering stencils (Sec. 3, Eq. staggered_finite_sum).
+psatd        Standard / Galilean / averaged-Galilean PSATD coefficients and
+             k-space updates (Sec. 4.2-4.4).
+particles    B-spline shapes, gather, Boris push, direct deposition, tile bins.
+step         The hybrid PIC cycle of Sec. 2.
+diagnostics  Field energy (Sec. 2 (iii)) and the L2 error norm (Sec. 5.2).
+
+Parity status: every function is pinned by tests/test_oracle_*.py against
+closed forms, brute force or invariants, except the full multi-step cycle,
+which is pinned only compositionally plus invariants (charge, cold-plasma
+oscillation, vacuum energy); beyond that the full step is "parity unpinned".
+"""

@@ -1,0 +1,97 @@
+"""Pins for oracle.particles: B-spline shapes, gather, deposit, Boris push, tile bins.
+
+Checked against: the Cox-de Boor recursion for centred B-splines (textbook,
+independent of the closed forms), partition of unity and linear
+reproduction, exact gathers of uniform/linear fields, gather/deposit
+adjointness, total charge, the analytic gyration of the Boris rotation and
+the exact pure-E kick, and a per-particle brute-force bin count.
+"""
+import numpy as np
+import pytest
+
+from oracle import particles
+
+
+def _bspline(p, x):
+    """Centred cardinal B-spline of degree p (support [-(p+1)/2, (p+1)/2]) by recursion."""
+    if p == 0:
+        return np.where((x >= -0.5) & (x < 0.5), 1.0, 0.0)
+    return ((x + (p + 1) / 2) * _bspline(p - 1, x + 0.5) + ((p + 1) / 2 - x) * _bspline(p - 1, x - 0.5)) / p
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_shape_weights_are_bsplines(order):
+    rng = np.random.default_rng(order)
+    x = rng.uniform(0, 20, 2000)
+    lo, w = particles.shape_weights(x, 1.0, order)
+    assert w.shape == (order + 1, x.size)
+    for n in range(order + 1):
+        np.testing.assert_allclose(w[n], _bspline(order, x - (lo + n)), atol=1e-14)
+    np.testing.assert_allclose(w.sum(axis=0), 1.0, atol=1e-14)                         # partition of unity
+    np.testing.assert_allclose(sum((lo + n) * w[n] for n in range(order + 1)), x, atol=1e-12)  # first moment
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_gather_uniform_and_linear_fields_exact(order):
+    shape, dx = (16, 16, 16), (0.5, 1.0, 2.0)
+    rng = np.random.default_rng(2)
+    pos = [rng.uniform(4 * dx[a], 11 * dx[a], 500) for a in range(3)]
+    X, Y, Z = np.meshgrid(*[np.arange(shape[a]) * dx[a] for a in range(3)], indexing="ij")
+    const = np.full(shape, 3.25)
+    lin = 0.3 * X - 1.1 * Y + 0.7 * Z + 2.0
+    gc, gl = particles.gather([const, lin], pos, dx, order)
+    np.testing.assert_allclose(gc, 3.25, atol=1e-13)
+    np.testing.assert_allclose(gl, 0.3 * pos[0] - 1.1 * pos[1] + 0.7 * pos[2] + 2.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_deposit_gather_adjoint_and_charge(order):
+    shape, dx = (8, 4, 8), (0.5, 1.0, 0.25)
+    rng = np.random.default_rng(4)
+    n = 3000
+    pos = [rng.uniform(0, shape[a] * dx[a], n) for a in range(3)]
+    v = rng.normal(size=n)
+    F = rng.normal(size=shape)
+    (rho,) = particles.deposit(shape, pos, [v], dx, order)
+    dV = dx[0] * dx[1] * dx[2]
+    (g,) = particles.gather([F], pos, dx, order)
+    assert abs(np.sum(rho * F) * dV - np.sum(v * g)) < 1e-10 * np.sum(np.abs(v * g))
+    assert abs(np.sum(rho) * dV - np.sum(v)) < 1e-11 * np.sum(np.abs(v))
+
+
+def test_boris_pure_magnetic_gyration():
+    # |u| conserved; rotation angle per step = 2 atan(q B dt / (2 m gamma)) about B
+    q, m, dt, Bz = -1.0, 1.0, 0.3, 2.0
+    u = [np.array([0.4]), np.array([0.0]), np.array([0.1])]
+    gamma = np.sqrt(1 + 0.4 ** 2 + 0.1 ** 2)
+    E = [np.zeros(1)] * 3
+    B = [np.zeros(1), np.zeros(1), np.full(1, Bz)]
+    un = particles.boris(u, E, B, q, m, dt)
+    ang = np.arctan2(un[1][0], un[0][0])
+    assert abs(np.hypot(un[0][0], un[1][0]) - 0.4) < 1e-15
+    assert un[2][0] == 0.1
+    # dv/dt = (q/m) v x B: for q B_z < 0 the rotation in the (x,y) plane is counter-clockwise
+    assert abs(ang - 2 * np.arctan(-q * Bz * dt / (2 * m * gamma))) < 1e-14
+
+
+def test_boris_pure_electric_kick():
+    q, m, dt = -1.0, 2.0, 0.1
+    u = [np.array([0.3]), np.array([-0.2]), np.array([0.0])]
+    E = [np.array([1.0]), np.array([2.0]), np.array([-0.5])]
+    B = [np.zeros(1)] * 3
+    un = particles.boris(u, E, B, q, m, dt)
+    for a in range(3):
+        assert abs(un[a][0] - (u[a][0] + q * E[a][0] * dt / m)) < 1e-16
+
+
+def test_tile_bins_brute_force():
+    shape, dx, tile = (16, 8, 24), (0.5, 1.0, 0.1), (8, 4, 8)
+    rng = np.random.default_rng(9)
+    pos = [rng.uniform(0, shape[a] * dx[a], 4000) for a in range(3)]
+    tid, off, order = particles.tile_bins(pos, dx, shape, tile)
+    nt = [shape[a] // tile[a] for a in range(3)]
+    for p in range(0, 4000, 37):
+        c = [int(pos[a][p] // dx[a]) for a in range(3)]
+        assert tid[p] == ((c[0] // tile[0]) * nt[1] + c[1] // tile[1]) * nt[2] + c[2] // tile[2]
+    assert off[0] == 0 and off[-1] == 4000 and len(off) == nt[0] * nt[1] * nt[2] + 1
+    assert np.all(np.diff(tid[order]) >= 0)

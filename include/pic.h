@@ -1,0 +1,277 @@
+/*
+ * libpic: hybrid nodal-staggered PSATD particle-in-cell step on one GB300.
+ *
+ * Method: Zoni et al., "A Hybrid Nodal-Staggered Pseudo-Spectral Electromagnetic
+ * Particle-In-Cell Method with Finite-Order Centering" (arXiv 2106.12919).
+ * One step follows the hybrid cycle of Sec. 2: gather E, B from a nodal grid,
+ * push particles, deposit J and rho on the nodal grid, center J to the Yee grid
+ * with finite-order Fornberg stencils (Sec. 3), solve Maxwell's equations on the
+ * Yee grid in Fourier space with a PSATD update (Sec. 4: standard, Galilean or
+ * averaged Galilean), and center E, B back to the nodal grid.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: SI-like with c and eps0 as parameters (mu0 = 1 / (eps0 c^2)).
+ * Grid: Nx x Ny x Nz cells, periodic on every axis, each N a power of two in
+ *   [8, 1024].  Node (i, j, k) is at (i dx, j dy, k dz).
+ * Real-space arrays: one array per component, C order [Nx][Ny][Nz] (z fastest),
+ *   element type double (PIC_FP64).  Yee positions (App. A): E^x, J^x at
+ *   (i+1/2, j, k); E^y, J^y at (i, j+1/2, k); E^z, J^z at (i, j, k+1/2);
+ *   B^x at (i, j+1/2, k+1/2); B^y at (i+1/2, j, k+1/2); B^z at (i+1/2, j+1/2, k);
+ *   rho nodal.  "Nodal" arrays hold every component at (i, j, k).
+ * Spectral arrays (only the FFT entry points expose them): complex interleaved
+ *   (re, im), C order [Nx][Ny][Nz/2+1], plain DFT sum_j f_j exp(-2 pi i j.m / N)
+ *   with no normalisation on the forward transform.
+ * Pointers: every field and particle pointer is DEVICE memory owned by the
+ *   caller, never freed or retained by the library; "host" pointers are named
+ *   as such.  Work buffers, coefficient tables and the spectral field state
+ *   belong to the context.
+ * Streams: all work is enqueued on the context's stream (pic_ext.cuda_stream,
+ *   default: the legacy default stream).  Calls return once the work is
+ *   enqueued, except those that return a host value (documented per call).
+ *   Kernel errors surface as PIC_ERR_CUDA at the next call or at pic_sync.
+ * Errors: every call returns a pic_status and never aborts; pic_last_error
+ *   gives a one-line description.  Arguments are validated before any launch.
+ * Threads: one context per host thread / stream at a time.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_ERR_ARG = -1,          /* invalid argument (null pointer, size, order, ...) */
+  PIC_ERR_UNSUPPORTED = -2,  /* valid but not implemented (e.g. grid size not a power of two) */
+  PIC_ERR_NOMEM = -3,        /* device allocation failed */
+  PIC_ERR_CUDA = -4,         /* a CUDA call or kernel failed */
+  PIC_ERR_CAPACITY = -5,     /* more particles than the context was sized for */
+  PIC_ERR_TIMEOUT = -6,      /* reserved: a bounded device-side wait gave up */
+  PIC_ERR_NONFINITE = -7     /* reserved: non-finite values detected */
+} pic_status;
+
+typedef enum {
+  PIC_PSATD_STANDARD = 0,          /* Sec. 4.2, Eqs. eq_update_B/E_with_rho_standard */
+  PIC_PSATD_GALILEAN = 1,          /* Sec. 4.3, Eqs. eq_update_B/E_with_rho_galilean */
+  PIC_PSATD_AVERAGED_GALILEAN = 2  /* Sec. 4.4, Eqs. eq_update_B/E_with_rho_averaged */
+} pic_variant;
+
+typedef enum { PIC_FP64 = 0 } pic_precision;
+
+/*
+ * Optional extension block (pass NULL for defaults).  struct_size must be
+ * sizeof(pic_ext) of the caller's header (versioning).
+ *   spectral_order[3]: order 2m of the modified wave numbers [k]_s, [k]_c of
+ *     Sec. 4.1 per axis; 0 = infinite order ([k] = k).  Default 0.
+ *   precision: PIC_FP64 (only value accepted).
+ *   c, eps0: speed of light and vacuum permittivity.  Defaults 1, 1.
+ *   tile[3]: particle tile edge in cells per axis for binning (powers of two
+ *     dividing the grid).  Default 8, 8, 8.
+ *   sort_interval: re-bin the particles every this many steps inside pic_step
+ *     (0 = never).  Default 20.
+ *   cuda_stream: a cudaStream_t; NULL = legacy default stream.
+ */
+typedef struct {
+  uint32_t struct_size;
+  int32_t spectral_order[3];
+  int32_t precision;
+  double c;
+  double eps0;
+  int32_t tile[3];
+  int32_t sort_interval;
+  void* cuda_stream;
+} pic_ext;
+
+/* Fill *ext with the defaults listed above. */
+void pic_ext_default(pic_ext* ext);
+
+/*
+ * pic_init: create a context for one grid and method configuration.
+ *   grid[3]             Nx, Ny, Nz (powers of two in [8, 1024]; else PIC_ERR_UNSUPPORTED).
+ *   dx[3]               cell sizes (> 0).
+ *   dt                  time step (> 0).
+ *   shape_order         particle shape: 1 (CIC), 2 (quadratic), 3 (cubic) B-spline
+ *                       on the nodal grid (Secs. 5.2-5.3 use cubic splines).
+ *   centering_order[3]  order 2m of the finite-order centering of Sec. 3 per axis
+ *                       (even, 2 <= 2m <= 32 and 2m <= N).
+ *   psatd_variant       a pic_variant.
+ *   v_gal[3]            Galilean velocity (ignored by PIC_PSATD_STANDARD; |v_gal| < c).
+ *   ext                 NULL or a pic_ext.
+ * Allocates the work buffers and builds the per-mode FP64 coefficient tables
+ * of Sec. 4 on the device.  On success *out is a new context (free it with
+ * pic_destroy); on failure *out is NULL.  Synchronous.
+ */
+pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], double dt,
+                    int shape_order, const int32_t centering_order[3], int psatd_variant,
+                    const double v_gal[3], const pic_ext* ext);
+
+void pic_destroy(pic_ctx* ctx);
+
+/* Last error message of this context (static storage owned by the context). */
+const char* pic_last_error(const pic_ctx* ctx);
+
+/* Wait for the context's stream; returns PIC_ERR_CUDA if any enqueued work failed. */
+pic_status pic_sync(pic_ctx* ctx);
+
+/*
+ * One particle species, device SoA of n particles (FP64 form).
+ *   x, y, z    positions in [0, N dx) per axis (Galilean coordinates for the
+ *              Galilean variants).
+ *   ux, uy, uz momentum per unit mass u = gamma v, at the half step u^{n-1/2}.
+ *   w          macro-particle weight (number of physical particles).
+ *   id         optional (may be NULL): an int64 tag per particle, permuted
+ *              together with the other arrays when the library re-bins.
+ *   q, m       charge and mass of one physical particle.
+ * The library may PERMUTE all arrays of a species in place (tile binning);
+ * the multiset of particles is unchanged.
+ */
+typedef struct {
+  int64_t n;
+  double q;
+  double m;
+  double* x;
+  double* y;
+  double* z;
+  double* ux;
+  double* uy;
+  double* uz;
+  double* w;
+  int64_t* id;
+} pic_species;
+
+/*
+ * pic_step: advance fields and particles by nsteps hybrid PIC steps (Sec. 2).
+ *   E[3], B[3]  in/out: Yee-grid fields at t^n on entry, t^{n+nsteps} on exit.
+ *   J[3]        out: J^{n+nsteps-1/2} on the Yee grid (centered from the nodal deposit).
+ *   rho         in/out: nodal rho^n on entry (see pic_deposit_rho), rho^{n+nsteps} on exit.
+ *   sp          n_species species (positions x^n, momenta u^{n-1/2} on entry).
+ * Per step: gather at x^n from the nodal E, B (Sec. 2); Boris push; move by
+ * dt (v - v_gal); direct deposition of J^{n+1/2} at x^{n+1/2} = (x^n + x^{n+1})/2
+ * and of rho^{n+1} at x^{n+1} (nodal); centering of J to the Yee grid (Sec. 3);
+ * PSATD update in Fourier space (Sec. 4); centering of E, B to the nodal grid.
+ * The centering stencils are applied as their exact Fourier symbol (App. C,
+ * zeta_F) inside the k-space update.  Averaged Galilean: the fields gathered at
+ * step n+1 are <E>^{n+1}, <B>^{n+1} (Sec. 4.4); the first step of each call
+ * gathers E, B.  Asynchronous.
+ */
+pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double* const J[3],
+                    double* rho, const pic_species* sp, int n_species, int nsteps);
+
+/*
+ * pic_deposit_rho: rho (nodal, overwritten) = sum over species of the direct
+ * charge deposition q w S(x - x_i) / dV at the current positions; use it to
+ * form rho^0 before the first pic_step.  Asynchronous.
+ */
+pic_status pic_deposit_rho(pic_ctx* ctx, const pic_species* sp, int n_species, double* rho);
+
+/*
+ * pic_push_deposit: one particle stage in isolation (gather + Boris + move +
+ * deposit) from caller-provided NODAL fields En[3], Bn[3]; J_nodal[3] and
+ * rho_nodal are overwritten with J^{n+1/2} and rho^{n+1} (nodal).  Particles
+ * are updated in place and not re-binned.  Asynchronous.
+ */
+pic_status pic_push_deposit(pic_ctx* ctx, const double* const En[3], const double* const Bn[3],
+                            const pic_species* sp, int n_species, double* const J_nodal[3],
+                            double* rho_nodal);
+
+/*
+ * pic_bin: tile binning of one species (spec design; the paper is silent).
+ * cell_a = floor(x_a * (1/dx_a)) mod N_a, tile_a = cell_a / tile_edge_a,
+ * tile id = (tile_x * nty + tile_y) * ntz + tile_z.  Permutes the species
+ * arrays in place so that tile ids are non-decreasing, and writes
+ * offsets[n_tiles + 1] (int64, device, exclusive prefix sum of the per-tile
+ * counts) if offsets is not NULL.  The order inside a tile is unspecified.
+ * n_tiles = prod(N_a / tile_edge_a).  Asynchronous.
+ */
+pic_status pic_bin(pic_ctx* ctx, const pic_species* sp, int64_t* offsets);
+
+/* Number of tiles of the context's tiling. */
+int64_t pic_num_tiles(const pic_ctx* ctx);
+
+/*
+ * pic_center_to_nodal: finite-order centering of the six Yee components
+ * F = {E^x, E^y, E^z, B^x, B^y, B^z} onto the nodal grid, as real-space stencils
+ * (Sec. 3, Eq. staggered_finite_sum) applied along each staggered axis of each
+ * component in x, y, z order, periodic wrap.  out[6] nodal, overwritten.
+ * Asynchronous.
+ */
+pic_status pic_center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);
+
+/*
+ * pic_center_to_yee: finite-order centering of nodal J^x, J^y, J^z onto their
+ * Yee positions, the mirror image of Eq. staggered_finite_sum:
+ * f_{j+1/2} = sum_n alpha^s_{m,n} (f_{j+n} + f_{j-n+1}) / 2 along the staggered
+ * axis of each component.  out[3] overwritten.  Asynchronous.
+ */
+pic_status pic_center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* const out[3]);
+
+/*
+ * pic_fft_forward / pic_fft_inverse: 3D real-to-complex DFT of ncomp real
+ * arrays (App. A.1, Eq. Fourier_discrete, without the half-cell phase) and its
+ * unnormalised inverse (complex-to-real; the imaginary parts of the k_z = 0 and
+ * k_z = Nyquist planes are ignored).  spec[c] points to a complex array of
+ * Nx*Ny*(Nz/2+1) (re, im) double pairs.  The inverse overwrites spec.
+ * 1 <= ncomp <= 6.  Asynchronous.
+ */
+pic_status pic_fft_forward(pic_ctx* ctx, const double* const real[], double* const spec[], int ncomp);
+pic_status pic_fft_inverse(pic_ctx* ctx, double* const spec[], double* const real[], int ncomp);
+
+/*
+ * pic_maxwell_step: the field solve of one step in isolation (Sec. 4):
+ * Yee E^n, B^n, J^{n+1/2} (Yee), rho^n, rho^{n+1} (nodal) -> Yee E^{n+1}, B^{n+1}
+ * (in place).  For the averaged variant, Eavg[3], Bavg[3] (may be NULL for the
+ * other variants) receive <E>^{n+1}, <B>^{n+1} at the Yee positions.
+ * Asynchronous.
+ */
+pic_status pic_maxwell_step(pic_ctx* ctx, double* const E[3], double* const B[3],
+                            const double* const J[3], const double* rho_n,
+                            const double* rho_np1, double* const Eavg[3], double* const Bavg[3]);
+
+/*
+ * pic_coefficient: copy one per-mode coefficient table (complex, layout of the
+ * spectral arrays) into out (device, Nx*Ny*(Nz/2+1) (re, im) pairs).  Names:
+ * "TC" = theta_c^2 C, "TS" = theta_c^2 S/omega_s, "X1", "X2", "TX3" = theta_c^2 X3,
+ * "X4" (Secs. 4.2-4.3), and for the averaged variant "Psi1", "Psi2", "Y1", "Y2",
+ * "Y3", "Y4" (Sec. 4.4).  Unknown name: PIC_ERR_ARG.  Asynchronous.
+ */
+pic_status pic_coefficient(pic_ctx* ctx, const char* name, double* out);
+
+/*
+ * pic_field_energy: W = 1/2 sum (eps0 |E|^2 + |B|^2 / mu0) dV over the cells with
+ * index in [box_lo, box_hi) per axis of each Yee component (Sec. 2 (iii); NULL
+ * box = whole grid), FP64 reduction; *out is a HOST double.  Synchronous.
+ */
+pic_status pic_field_energy(pic_ctx* ctx, const double* const E[3], const double* const B[3],
+                            const int64_t box_lo[3], const int64_t box_hi[3], double* out);
+
+/* pic_total_charge: sum(rho) dV of a nodal array; *out is a HOST double.  Synchronous. */
+pic_status pic_total_charge(pic_ctx* ctx, const double* rho, double* out);
+
+/*
+ * pic_timing: enable (1) or disable (0) per-stage device timing and reset the
+ * accumulators.  When enabled, each stage call of pic_step records a pair of
+ * CUDA events on the context stream.  Stages: "push" (gather + Boris + deposit),
+ * "fft", "update" (fused PSATD k-space update), "bin" (tile binning), "other"
+ * (phase, centering-symbol and diagnostic kernels).  Kernel launches are
+ * counted per stage whether or not timing is enabled.  Synchronous.
+ */
+pic_status pic_timing(pic_ctx* ctx, int enable);
+
+/*
+ * pic_timing_read: total device time in ms (*ms, HOST) and kernel launches
+ * (*launches, HOST) of one stage since the last pic_timing call; stage "all"
+ * gives the launch total and the summed time.  Synchronous.
+ */
+pic_status pic_timing_read(pic_ctx* ctx, const char* stage, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,176 @@
+// Internal declarations of libpic (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+
+#include "pic.h"
+
+#define PIC_MAX_CENTER_M 16  // centering order 2m <= 32
+
+// ---------------------------------------------------------------------------
+// complex helpers (double2 / float2 as (re, im))
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmake(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cmuli(double2 a) { return make_double2(-a.y, a.x); }  // i * a
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// Index of a coefficient table inside pic_ctx::coef.
+enum CoefIdx {
+  COEF_TC = 0, COEF_TS, COEF_X1, COEF_X2, COEF_TX3, COEF_X4,
+  COEF_PSI1, COEF_PSI2, COEF_Y1, COEF_Y2, COEF_Y3, COEF_Y4, COEF_COUNT
+};
+
+// Finite-order centering weights alpha^s_{m,n}/2 of one axis (Sec. 3).
+struct CenterWeights {
+  int m;
+  double w[PIC_MAX_CENTER_M];
+};
+
+// Per-stage device timing (CUDA events on the context stream) and launch counts.
+enum TimerStage { STAGE_PUSH = 0, STAGE_FFT, STAGE_UPDATE, STAGE_BIN, STAGE_OTHER, STAGE_COUNT };
+struct Timers {
+  int on;
+  int pool_size;
+  int used;
+  cudaEvent_t* pool;   // pairs (start, stop)
+  int* stage;          // stage of each pair
+  int64_t launches[STAGE_COUNT];
+};
+
+struct pic_ctx {
+  // configuration
+  int64_t N[3];
+  double dx[3];
+  double dt;
+  int shape_order;
+  int corder[3];
+  int variant;
+  double vg[3];
+  int sorder[3];
+  double c, eps0;
+  int tile[3];
+  int sort_interval;
+  cudaStream_t stream;
+  int64_t ncell, nzh, nmode;
+  int ncoef;
+  CenterWeights cw[3];
+
+  // device tables
+  double* k1d;       // [3][Nmax] ks, then [3][Nmax] kc, then [3][Nmax] zeta
+  double* ks[3];
+  double* kc[3];
+  double* zeta[3];
+  double2* twid[3];  // twiddles exp(-2 pi i j / N_a), j < N_a
+  double2* coef;     // [ncoef][nmode]
+
+  // spectral state and work (paper-convention spectra)
+  double2* EBh;      // [6][nmode]: E^x..E^z, B^x..B^z
+  double2* rhoh[2];  // rho^n, rho^{n+1}
+  double2* Jh;       // [3][nmode]
+  double2* G;        // [6][nmode] scratch for inverse transforms
+
+  // real-space work
+  double* nodal;     // [6][ncell] nodal gather fields
+  double* Jn;        // [3][ncell] nodal J deposit
+
+  // binning scratch (grown on demand)
+  int64_t bin_cap;
+  int32_t* bin_tid;
+  int64_t* bin_counts;   // [n_tiles + 1]
+  int64_t* bin_cursor;   // [n_tiles]
+  double* bin_tmp;       // [8][bin_cap] permuted copies
+  void* scan_tmp;
+  size_t scan_tmp_bytes;
+  int64_t n_tiles;
+
+  int64_t steps_done;
+  Timers timers;
+  char err[256];
+};
+
+// RAII stage scope: counts `launches` kernel launches for the stage and, when timing is on,
+// brackets the enclosed work with a pair of events on the context stream.
+struct StageScope {
+  pic_ctx* ctx;
+  int pair;
+  StageScope(pic_ctx* c, int stage, int launches);
+  ~StageScope();
+};
+void timers_free(pic_ctx* ctx);
+
+// error helpers --------------------------------------------------------------
+pic_status pic_set_error(pic_ctx* ctx, pic_status st, const char* fmt, ...);
+#define PIC_CUDA_TRY(ctx, call)                                                      \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return pic_set_error((ctx), PIC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+#define PIC_LAUNCH_CHECK(ctx)                                                        \
+  do {                                                                               \
+    cudaError_t e_ = cudaGetLastError();                                             \
+    if (e_ != cudaSuccess)                                                           \
+      return pic_set_error((ctx), PIC_ERR_CUDA, "launch at %s:%d: %s", __FILE__, __LINE__, \
+                           cudaGetErrorString(e_));                                  \
+  } while (0)
+
+// Real-space component pointer bundles passed by value to kernels.
+struct RPtr6 { double* p[6]; };
+struct CRPtr6 { const double* p[6]; };
+struct CPtr6 { double2* p[6]; };
+
+// fft.cu ---------------------------------------------------------------------
+pic_status fft_setup(pic_ctx* ctx);
+// Forward R2C of ncomp real arrays into spectral arrays (plain DFT, unnormalised).
+pic_status fft_r2c(pic_ctx* ctx, CRPtr6 in, CPtr6 out, int ncomp);
+// Inverse C2R (unnormalised); spectral arrays are destroyed.
+pic_status fft_c2r(pic_ctx* ctx, CPtr6 in, RPtr6 out, int ncomp);
+
+// psatd.cu -------------------------------------------------------------------
+pic_status psatd_setup(pic_ctx* ctx);   // 1D tables + per-mode coefficient tables
+// Spectral update of one step. Reads ctx->EBh, ctx->Jh (nodal DFT of J), rhoh[cur], rhoh[1-cur];
+// writes EBh (n+1), Jh (Yee-centered, paper convention) and G = Z * (E or <E>, B or <B>) / Ncell.
+pic_status psatd_update(pic_ctx* ctx, int cur);
+// General form: g_mode 0 -> G = zeta (E,B) / Ncell (nodal), 1 -> G = shift^+ (E,B) / Ncell (Yee);
+// j_yee: Jh already holds the Yee-centered paper-convention spectrum; write_j: store it back.
+pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
+                           int write_j);
+// Multiply spectral arrays (plain DFT) by the staggering phase of each component:
+// sign = -1: plain DFT -> paper convention; +1: paper convention -> plain DFT (times scale).
+// comp_kind[c]: 0..5 = Ex..Bz, 6..8 = Jx..Jz, 9 = rho.
+pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, int ncomp, int sign,
+                       double scale);
+// G[c] = Z_c * src[c] * scale, src = the six E,B spectra given (paper convention) -> nodal DFT.
+pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale);
+
+// particles.cu ----------------------------------------------------------------
+pic_status particles_push(pic_ctx* ctx, const double* const En[3], const double* const Bn[3],
+                          const pic_species* sp, double* const J[3], double* rho);
+pic_status particles_deposit_rho(pic_ctx* ctx, const pic_species* sp, double* rho);
+pic_status particles_bin(pic_ctx* ctx, const pic_species* sp, int64_t* offsets_out);
+
+// center.cu -------------------------------------------------------------------
+pic_status center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);
+pic_status center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* const out[3]);
+
+// diag.cu ---------------------------------------------------------------------
+pic_status diag_energy(pic_ctx* ctx, const double* const E[3], const double* const B[3],
+                       const int64_t lo[3], const int64_t hi[3], double* out);
+pic_status diag_sum(pic_ctx* ctx, const double* a, double* out);
+
+// Exact-reduction sin/cos of pi * p / q for integers (host), used to build tables.
+void sincospi_frac(int64_t p, int64_t q, double* s, double* c);

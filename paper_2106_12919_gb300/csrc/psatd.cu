@@ -1,0 +1,622 @@
+// PSATD coefficient tables and the fused k-space update (Sec. 4).
+//
+// Per-mode coefficients are built once, on the device, in FP64.  The paper's
+// closed forms (Secs. 4.2-4.4) are 0/0 at omega_s = 0 and Omega_c = 0 and lose
+// digits near those points and near omega_s = |Omega_c|, so every coefficient
+// is evaluated from an equivalent integral representation of the analytic
+// solution (the same ODE the paper integrates in App. A):
+//   K1(phi, a) = int_0^1 sigma sinc(phi sigma) e^{i a sigma} d sigma        (X1 = dt^2/eps0 K1)
+//   K2(phi, a) = (K1(phi,a) - e^{ia} K1(phi,0)) / (1 - e^{ia})               (X2 = c^2 dt^2/eps0 K2)
+//   K3(phi, a) = e^{ia} (K1(phi,a) - K1(phi,0)) / (1 - e^{ia})              (theta^2 X3 = c^2 dt^2/eps0 K3)
+// with phi = omega_s dt, a = Omega_c dt, and for the averaged fields the time
+// average over [t^{n+1/2}, t^{n+3/2}] of the same solution.  Where the closed
+// forms in terms of E(b) = int_0^1 e^{ib s} ds, F(b) = int_{1/2}^{3/2} e^{ib s} ds
+// and H(b) = int_{1/2}^{3/2} int_0^s e^{ibu} du ds are well conditioned
+// (phi >= 0.3 and |a| >= 0.3) they are used; elsewhere the integrals are taken
+// by 16-point Gauss-Legendre quadrature of stable integrands (entire functions
+// of modest frequency, so the rule is exact to rounding).  a = 0 uses the
+// standard forms (Sec. 4.2) directly.
+#include "pic_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace {
+
+constexpr int kGL = 16;
+struct GaussLegendre {
+  double x[kGL];  // nodes on [0, 1]
+  double w[kGL];  // weights, sum 1
+};
+
+// ---------------------------------------------------------------------------
+// scalar helpers (device)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sinc_d(double x) {
+  const double ax = fabs(x);
+  if (ax < 1e-3) {
+    const double x2 = x * x;
+    return 1.0 - x2 * (1.0 / 6.0) + x2 * x2 * (1.0 / 120.0);
+  }
+  return sin(x) / x;
+}
+__device__ __forceinline__ double2 cis(double t) {
+  double s, c;
+  sincos(t, &s, &c);
+  return make_double2(c, s);
+}
+// (x - sin x) / x^3
+__device__ double k2s(double x) {
+  if (fabs(x) < 0.5) {
+    const double x2 = x * x;
+    double term = 1.0 / 6.0, sum = term;
+    for (int n = 2; n <= 12; ++n) {  // (-1)^{n+1} x^{2n-2} / (2n+1)!
+      term *= -x2 / ((2.0 * n) * (2.0 * n + 1.0));
+      sum += term;
+    }
+    return sum;
+  }
+  return (x - sin(x)) / (x * x * x);
+}
+// (x cos x - sin x) / x^3
+__device__ double k3s(double x) {
+  if (fabs(x) < 0.5) {
+    const double x2 = x * x;
+    // sum_{n>=1} (-1)^n 2n / (2n+1)! x^{2n-2}
+    double f = 1.0 / 6.0;  // 1/(2n+1)! at n = 1
+    double p = 1.0;        // x^{2n-2}
+    double sum = 0.0;
+    for (int n = 1; n <= 12; ++n) {
+      if (n > 1) {
+        f /= (2.0 * n) * (2.0 * n + 1.0);
+        p *= x2;
+      }
+      sum += ((n & 1) ? -1.0 : 1.0) * 2.0 * n * f * p;
+    }
+    return sum;
+  }
+  double s, c;
+  sincos(x, &s, &c);
+  return (x * c - s) / (x * x * x);
+}
+// K1(phi, 0) = (1 - cos phi) / phi^2 = sinc(phi/2)^2 / 2
+__device__ __forceinline__ double k1s(double x) {
+  const double s = sinc_d(0.5 * x);
+  return 0.5 * s * s;
+}
+// E(b) = e^{ib/2} sinc(b/2)
+__device__ __forceinline__ double2 Eint(double b) { return cscale(cis(0.5 * b), sinc_d(0.5 * b)); }
+// F(b) = e^{ib} sinc(b/2)
+__device__ __forceinline__ double2 Fint(double b) { return cscale(cis(b), sinc_d(0.5 * b)); }
+// H(b) = (F(b) - 1) / (i b); series sum_n (ib)^n / (n+1)! M_{n+1}, M_p = ((3/2)^{p+1} - (1/2)^{p+1})/(p+1)
+__device__ double2 Hint(double b) {
+  if (fabs(b) < 0.5) {
+    double2 p = make_double2(1.0, 0.0);  // (ib)^n / (n+1)!
+    double2 sum = make_double2(0.0, 0.0);
+    double a3 = 1.5 * 1.5, a1 = 0.25;     // (3/2)^{n+2}, (1/2)^{n+2}
+    for (int n = 0; n <= 22; ++n) {
+      if (n > 0) {
+        p = cscale(cmuli(cscale(p, b)), 1.0 / (n + 1.0));
+        a3 *= 1.5;
+        a1 *= 0.5;
+      }
+      const double M = (a3 - a1) / (n + 2.0);
+      sum = cadd(sum, cscale(p, M));
+    }
+    return sum;
+  }
+  const double2 f = Fint(b);
+  return cdiv(make_double2(f.x - 1.0, f.y), make_double2(0.0, b));
+}
+// h(u) = (e^{iau} - 1) / (e^{ia} - 1) = e^{ia(u-1)/2} u sinc(au/2) / sinc(a/2)
+__device__ __forceinline__ double2 hfun(double a, double u) {
+  return cscale(cis(0.5 * a * (u - 1.0)), u * sinc_d(0.5 * a * u) / sinc_d(0.5 * a));
+}
+
+struct Coefs {
+  double2 v[COEF_COUNT];
+};
+
+// All coefficients of one mode.  phi = omega_s dt >= 0, a = Omega_c dt.
+__device__ Coefs mode_coefs(double phi, double a, bool averaged, double dt, double c, double eps0,
+                            const GaussLegendre& gl) {
+  Coefs r;
+  const double dt2e = dt * dt / eps0, c2dt2e = c * c * dt * dt / eps0;
+  const double sphi = sinc_d(phi), cphi = cos(phi);
+  const bool wc = phi >= 0.3 && fabs(a) >= 0.3;
+  double2 K1, K2, K3;
+  const double2 ea = cis(a);
+  if (a == 0.0) {
+    K1 = make_double2(k1s(phi), 0.0);
+    K2 = make_double2(k2s(phi), 0.0);
+    K3 = make_double2(k3s(phi), 0.0);
+  } else if (wc) {
+    K1 = cdiv(csub(Eint(a + phi), Eint(a - phi)), make_double2(0.0, 2.0 * phi));
+    const double K10 = k1s(phi);
+    const double2 den = make_double2(1.0 - ea.x, -ea.y);
+    K2 = cdiv(csub(K1, cscale(ea, K10)), den);
+    K3 = cdiv(cmul(ea, make_double2(K1.x - K10, K1.y)), den);
+  } else {
+    K1 = K2 = K3 = make_double2(0.0, 0.0);
+    const double sa = sinc_d(0.5 * a);
+    for (int q = 0; q < kGL; ++q) {
+      const double s = gl.x[q], w = gl.w[q];
+      const double g = s * sinc_d(phi * s);  // sin(phi s) / phi
+      K1 = cadd(K1, cscale(cis(a * s), w * g));
+      K2 = cadd(K2, cscale(cis(0.5 * a * s), w * g * (1.0 - s) * sinc_d(0.5 * a * (1.0 - s)) / sa));
+      K3 = csub(K3, cscale(cis(0.5 * a * (1.0 + s)), w * g * s * sinc_d(0.5 * a * s) / sa));
+    }
+  }
+  r.v[COEF_TC] = cscale(ea, cphi);
+  r.v[COEF_TS] = cscale(ea, dt * sphi);
+  r.v[COEF_X1] = cscale(K1, dt2e);
+  r.v[COEF_X2] = cscale(K2, c2dt2e);
+  r.v[COEF_TX3] = cscale(K3, c2dt2e);
+  // X4 = (dt/eps0) (i a K1 - e^{ia} sinc phi)
+  r.v[COEF_X4] = cscale(csub(cscale(cmuli(K1), a), cscale(ea, sphi)), dt / eps0);
+  if (!averaged) return r;
+
+  // averaged fields: <f> = int_{1/2}^{3/2} f(sigma dt) d sigma
+  const double2 Psi1 = cscale(cadd(Fint(a + phi), Fint(a - phi)), 0.5);
+  const double2 Psi3 = Fint(a);
+  double2 Psi2n, Y1n, Qn;  // Psi2 = -dt Psi2n, Y1 = dt^2/eps0 Y1n, <Q> = dt^2 Qn
+  if (wc) {
+    const double2 den2 = make_double2(0.0, 2.0 * phi);
+    Psi2n = cdiv(csub(Fint(a + phi), Fint(a - phi)), den2);
+    Y1n = cdiv(csub(Hint(a + phi), Hint(a - phi)), den2);
+    const double2 num = csub(cscale(csub(Psi3, Psi1), 1.0 / (phi * phi)), Y1n);
+    Qn = cdiv(num, make_double2(ea.x - 1.0, ea.y));
+  } else {
+    Psi2n = Y1n = Qn = make_double2(0.0, 0.0);
+    for (int q = 0; q < kGL; ++q) {
+      const double s = 0.5 + gl.x[q], w = gl.w[q];
+      Psi2n = cadd(Psi2n, cscale(cis(a * s), w * s * sinc_d(phi * s)));
+      double2 R = make_double2(0.0, 0.0), Q = make_double2(0.0, 0.0);
+      for (int p = 0; p < kGL; ++p) {
+        const double u = s * gl.x[p], wu = s * gl.w[p];
+        R = cadd(R, cscale(cis(a * u), wu * u * sinc_d(phi * u)));
+        if (a != 0.0) {
+          const double d = s - u;
+          Q = cadd(Q, cscale(cmul(cis(a * d), hfun(a, u)), wu * d * sinc_d(phi * d)));
+        }
+      }
+      Y1n = cadd(Y1n, cscale(R, w));
+      if (a != 0.0) Qn = cadd(Qn, cscale(Q, w));
+    }
+  }
+  double2 Y2, Y3;
+  if (a == 0.0) {
+    // rho linear in time: Y2 = -i c^2/eps0 <int_0^t G(t-s) s/dt ds>, Y3 = -i c^2/eps0 <int_0^t G (1 - s/dt)>
+    double A0 = 0.0, A1 = 0.0;
+    for (int q = 0; q < kGL; ++q) {
+      const double s = 0.5 + gl.x[q], w = gl.w[q];
+      A0 += w * s * s * k1s(phi * s);
+      A1 += w * s * s * s * k2s(phi * s);
+    }
+    Y2 = make_double2(0.0, -c2dt2e * A1);
+    Y3 = make_double2(0.0, -c2dt2e * (A0 - A1));
+  } else {
+    Y2 = cscale(cmuli(Qn), -c2dt2e);
+    Y3 = cscale(cmuli(csub(Y1n, Qn)), -c2dt2e);
+  }
+  r.v[COEF_PSI1] = Psi1;
+  r.v[COEF_PSI2] = cscale(Psi2n, -dt);
+  r.v[COEF_Y1] = cscale(Y1n, dt2e);
+  r.v[COEF_Y2] = Y2;
+  r.v[COEF_Y3] = Y3;
+  // Y4 = i Omega_c Y1 + Psi2 / eps0 = (dt/eps0) (i a Y1n - Psi2n)
+  r.v[COEF_Y4] = cscale(csub(cscale(cmuli(Y1n), a), Psi2n), dt / eps0);
+  return r;
+}
+
+struct TableArgs {
+  const double* ks[3];
+  const double* kc[3];
+  int64_t Ny, nzh, nmode;
+  double vg[3];
+  double dt, c, eps0;
+  int ncoef;
+  int averaged;
+  double2* coef;
+  GaussLegendre gl;
+};
+
+__global__ void build_tables_kernel(TableArgs t) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= t.nmode) return;
+  const int64_t iz = m % t.nzh, r = m / t.nzh;
+  const int64_t iy = r % t.Ny, ix = r / t.Ny;
+  const double kx = t.ks[0][ix], ky = t.ks[1][iy], kz = t.ks[2][iz];
+  const double phi = t.c * sqrt(kx * kx + ky * ky + kz * kz) * t.dt;
+  const double a = (t.vg[0] * t.kc[0][ix] + t.vg[1] * t.kc[1][iy] + t.vg[2] * t.kc[2][iz]) * t.dt;
+  const Coefs cf = mode_coefs(phi, a, t.averaged != 0, t.dt, t.c, t.eps0, t.gl);
+  for (int k = 0; k < t.ncoef; ++k) t.coef[k * t.nmode + m] = cf.v[k];
+}
+
+// ---------------------------------------------------------------------------
+// fused update
+// ---------------------------------------------------------------------------
+struct UpdArgs {
+  double2* EB;          // [6][nmode] in/out
+  double2* J;           // [3][nmode] in: DFT of the nodal (or Yee, j_yee) deposit; out: Yee-centered
+  const double2* rn;    // rho^n
+  const double2* rp;    // rho^{n+1}
+  const double2* coef;  // [ncoef][nmode]
+  double2* G;           // [6][nmode] out
+  const double* ks[3];
+  const double* zt[3];
+  const double2* hs[3];  // half-cell shifts exp(-i k dx / 2)
+  int64_t Ny, nzh, nmode;
+  double c2;
+  double gscale;
+  int g_mode;   // 0: G = Z (E, B) * gscale (nodal DFT); 1: G = shift^+ (E, B) * gscale (Yee DFT)
+  int j_yee;    // 1: J already Yee-centered paper-convention spectrum (skip zeta)
+  int write_j;  // write the Yee-centered J back
+};
+
+__device__ __forceinline__ double2 ld(const double2* p) { return __ldg(p); }
+
+template <int VAR>
+__global__ void __launch_bounds__(256) update_kernel(UpdArgs u) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= u.nmode) return;
+  const int64_t nm = u.nmode;
+  const int64_t iz = m % u.nzh, r = m / u.nzh;
+  const int64_t iy = r % u.Ny, ix = r / u.Ny;
+  const double k[3] = {u.ks[0][ix], u.ks[1][iy], u.ks[2][iz]};
+  const double zx = u.zt[0][ix], zy = u.zt[1][iy], zz = u.zt[2][iz];
+  double2 E[3], B[3], J[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    E[a] = u.EB[a * nm + m];
+    B[a] = u.EB[(3 + a) * nm + m];
+    J[a] = u.J[a * nm + m];
+  }
+  if (!u.j_yee) {
+    J[0] = cscale(J[0], zx);
+    J[1] = cscale(J[1], zy);
+    J[2] = cscale(J[2], zz);
+  }
+  const double2 rn = ld(u.rn + m), rp = ld(u.rp + m);
+  // [k] x F
+  auto cross = [&](const double2* F, double2* o) {
+    o[0] = csub(cscale(F[2], k[1]), cscale(F[1], k[2]));
+    o[1] = csub(cscale(F[0], k[2]), cscale(F[2], k[0]));
+    o[2] = csub(cscale(F[1], k[0]), cscale(F[0], k[1]));
+  };
+  double2 kE[3], kB[3], kJ[3];
+  cross(E, kE);
+  cross(B, kB);
+  cross(J, kJ);
+  const double2 TC = ld(u.coef + COEF_TC * nm + m), TS = ld(u.coef + COEF_TS * nm + m);
+  const double2 X1 = ld(u.coef + COEF_X1 * nm + m), X2 = ld(u.coef + COEF_X2 * nm + m);
+  const double2 TX3 = ld(u.coef + COEF_TX3 * nm + m), X4 = ld(u.coef + COEF_X4 * nm + m);
+  // rho term: i (theta^2 X3 rho^n - X2 rho^{n+1})
+  const double2 rterm = cmuli(csub(cmul(TX3, rn), cmul(X2, rp)));
+  double2 En[3], Bn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // B^{n+1} = TC B - i TS [k]xE + i X1 [k]xJ
+    Bn[a] = cadd(cmul(TC, B[a]), cmuli(csub(cmul(X1, kJ[a]), cmul(TS, kE[a]))));
+    // E^{n+1} = TC E + i c^2 TS [k]xB + X4 J + rterm [k]
+    En[a] = cadd(cadd(cmul(TC, E[a]), cmuli(cscale(cmul(TS, kB[a]), u.c2))),
+                 cadd(cmul(X4, J[a]), cscale(rterm, k[a])));
+  }
+  double2 Ga[3], Gb[3];
+  if (VAR == 2) {
+    const double2 P1 = ld(u.coef + COEF_PSI1 * nm + m), P2 = ld(u.coef + COEF_PSI2 * nm + m);
+    const double2 Y1 = ld(u.coef + COEF_Y1 * nm + m), Y2 = ld(u.coef + COEF_Y2 * nm + m);
+    const double2 Y3 = ld(u.coef + COEF_Y3 * nm + m), Y4 = ld(u.coef + COEF_Y4 * nm + m);
+    const double2 yr = cadd(cmul(Y3, rn), cmul(Y2, rp));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      // <B> = Psi1 B + i Psi2 [k]xE + i Y1 [k]xJ
+      Gb[a] = cadd(cmul(P1, B[a]), cmuli(cadd(cmul(P2, kE[a]), cmul(Y1, kJ[a]))));
+      // <E> = Psi1 E - i c^2 Psi2 [k]xB + Y4 J + (Y3 rho^n + Y2 rho^{n+1}) [k]
+      Ga[a] = cadd(csub(cmul(P1, E[a]), cmuli(cscale(cmul(P2, kB[a]), u.c2))),
+                   cadd(cmul(Y4, J[a]), cscale(yr, k[a])));
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Ga[a] = En[a];
+      Gb[a] = Bn[a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u.EB[a * nm + m] = En[a];
+    u.EB[(3 + a) * nm + m] = Bn[a];
+  }
+  if (u.write_j) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u.J[a * nm + m] = J[a];
+  }
+  const double s = u.gscale;
+  if (u.g_mode == 0) {
+    u.G[0 * nm + m] = cscale(Ga[0], zx * s);
+    u.G[1 * nm + m] = cscale(Ga[1], zy * s);
+    u.G[2 * nm + m] = cscale(Ga[2], zz * s);
+    u.G[3 * nm + m] = cscale(Gb[0], zy * zz * s);
+    u.G[4 * nm + m] = cscale(Gb[1], zx * zz * s);
+    u.G[5 * nm + m] = cscale(Gb[2], zx * zy * s);
+  } else {
+    const double2 hx = cconj(u.hs[0][ix]), hy = cconj(u.hs[1][iy]), hz = cconj(u.hs[2][iz]);
+    u.G[0 * nm + m] = cscale(cmul(Ga[0], hx), s);
+    u.G[1 * nm + m] = cscale(cmul(Ga[1], hy), s);
+    u.G[2 * nm + m] = cscale(cmul(Ga[2], hz), s);
+    u.G[3 * nm + m] = cscale(cmul(Gb[0], cmul(hy, hz)), s);
+    u.G[4 * nm + m] = cscale(cmul(Gb[1], cmul(hx, hz)), s);
+    u.G[5 * nm + m] = cscale(cmul(Gb[2], cmul(hx, hy)), s);
+  }
+}
+
+// staggering of each component kind: 0..5 = Ex..Bz, 6..8 = Jx..Jz, 9 = rho
+__host__ __device__ __forceinline__ int stag_mask(int kind) {
+  switch (kind) {
+    case 0: case 6: return 1;   // x
+    case 1: case 7: return 2;   // y
+    case 2: case 8: return 4;   // z
+    case 3: return 2 | 4;       // Bx: y, z
+    case 4: return 1 | 4;       // By: x, z
+    case 5: return 1 | 2;       // Bz: x, y
+    default: return 0;
+  }
+}
+
+struct PhaseArgs {
+  CPtr6 in, out;
+  int mask[6];
+  int sign;
+  double scale;
+  const double2* hs[3];
+  int64_t Ny, nzh, nmode;
+};
+
+__global__ void phase_kernel(PhaseArgs p) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= p.nmode) return;
+  const int c = blockIdx.y;
+  const int64_t iz = m % p.nzh, r = m / p.nzh;
+  const int64_t iy = r % p.Ny, ix = r / p.Ny;
+  double2 f = make_double2(p.scale, 0.0);
+  const int mk = p.mask[c];
+  if (mk & 1) f = cmul(f, p.hs[0][ix]);
+  if (mk & 2) f = cmul(f, p.hs[1][iy]);
+  if (mk & 4) f = cmul(f, p.hs[2][iz]);
+  if (p.sign > 0) f.y = -f.y;
+  p.out.p[c][m] = cmul(p.in.p[c][m], f);
+}
+
+struct NodalArgs {
+  const double2* EB;
+  double2* G;
+  const double* zt[3];
+  int64_t Ny, nzh, nmode;
+  double scale;
+};
+
+__global__ void to_nodal_kernel(NodalArgs a) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= a.nmode) return;
+  const int c = blockIdx.y;
+  const int64_t iz = m % a.nzh, r = m / a.nzh;
+  const int64_t iy = r % a.Ny, ix = r / a.Ny;
+  const int mk = stag_mask(c);
+  double z = a.scale;
+  if (mk & 1) z *= a.zt[0][ix];
+  if (mk & 2) z *= a.zt[1][iy];
+  if (mk & 4) z *= a.zt[2][iz];
+  a.G[c * a.nmode + m] = cscale(a.EB[c * a.nmode + m], z);
+}
+
+// ---------------------------------------------------------------------------
+// host-side table construction (1D, exact rationals are not needed at FP64)
+// ---------------------------------------------------------------------------
+long double factl(int n) {
+  long double f = 1.0L;
+  for (int i = 2; i <= n; ++i) f *= (long double)i;
+  return f;
+}
+// alpha^s_{m,n} (Eq. eq_Fornberg_staggered)
+long double alpha_s(int m, int n) {
+  long double dfact = 1.0L;  // (2m)! / (2^{2m} m!) = prod_{i=1}^m (2i-1)/2
+  for (int i = 1; i <= m; ++i) dfact *= (2.0L * i - 1.0L) / 2.0L;
+  const long double sgn = (n % 2 == 1) ? 1.0L : -1.0L;
+  return sgn * dfact * dfact * 4.0L / ((2.0L * n - 1.0L) * factl(m - n) * factl(m + n - 1));
+}
+// alpha^c_{m,n} (Eq. eq_Fornberg_centered)
+long double alpha_c(int m, int n) {
+  const long double sgn = (n % 2 == 1) ? 1.0L : -1.0L;
+  return sgn * 2.0L * factl(m) * factl(m) / (factl(m - n) * factl(m + n));
+}
+
+void gauss_legendre(GaussLegendre* g) {
+  // Newton iteration on P_n in long double; nodes mapped to [0, 1], weights halved.
+  const int n = kGL;
+  const long double pi = 3.14159265358979323846264338327950288L;
+  for (int i = 0; i < n; ++i) {
+    long double x = cosl(pi * (i + 0.75L) / (n + 0.5L));
+    long double dp = 0.0L;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1.0L, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0L);
+      const long double dx = p1 / dp;
+      x -= dx;
+      if (fabsl(dx) < 1e-30L) break;
+    }
+    {
+      long double p0 = 1.0L, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0L);
+    }
+    const long double w = 2.0L / ((1.0L - x * x) * dp * dp);
+    g->x[i] = (double)(0.5L * (1.0L - x));
+    g->w[i] = (double)(0.5L * w);
+  }
+}
+
+}  // namespace
+
+pic_status psatd_setup(pic_ctx* ctx) {
+  int64_t Nmax = std::max(ctx->N[0], std::max(ctx->N[1], ctx->N[2]));
+  std::vector<double> h(9 * Nmax, 0.0);
+  std::vector<double2> hs(3 * Nmax);
+  for (int a = 0; a < 3; ++a) {
+    const int64_t N = ctx->N[a];
+    const double dx = ctx->dx[a];
+    const int ms = ctx->sorder[a] / 2, mc = ctx->corder[a] / 2;
+    for (int64_t j = 0; j < N; ++j) {
+      const int64_t js = j < N / 2 ? j : j - N;  // signed index, Nyquist -> -N/2
+      double ks, kc, zeta = 0.0;
+      if (ms == 0) {
+        ks = kc = (double)(2.0L * 3.14159265358979323846264338327950288L * (long double)js / ((long double)N * dx));
+      } else {
+        long double sks = 0.0L, skc = 0.0L;
+        for (int n = 1; n <= ms; ++n) {
+          double s, c;
+          sincospi_frac(js * (2 * n - 1), N, &s, &c);  // sin(k (n - 1/2) dx)
+          sks += alpha_s(ms, n) * (long double)s / ((n - 0.5L) * dx);
+          sincospi_frac(2 * js * n, N, &s, &c);        // sin(k n dx)
+          skc += alpha_c(ms, n) * (long double)s / ((long double)n * dx);
+        }
+        ks = (double)sks;
+        kc = (double)skc;
+      }
+      long double sz = 0.0L;
+      for (int n = 1; n <= mc; ++n) {
+        double s, c;
+        sincospi_frac(js * (2 * n - 1), N, &s, &c);  // cos(k (n - 1/2) dx)
+        sz += alpha_s(mc, n) * (long double)c;
+      }
+      zeta = (double)sz;
+      h[(0 + a) * Nmax + j] = ks;
+      h[(3 + a) * Nmax + j] = kc;
+      h[(6 + a) * Nmax + j] = zeta;
+      double s, c;
+      sincospi_frac(js, N, &s, &c);  // k dx / 2 = pi js / N
+      hs[a * Nmax + j] = make_double2(c, -s);
+    }
+    ctx->cw[a].m = mc;
+    for (int n = 1; n <= mc; ++n) ctx->cw[a].w[n - 1] = (double)(alpha_s(mc, n) / 2.0L);
+  }
+  PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->k1d, 9 * Nmax * sizeof(double) + 3 * Nmax * sizeof(double2)));
+  PIC_CUDA_TRY(ctx, cudaMemcpy(ctx->k1d, h.data(), 9 * Nmax * sizeof(double), cudaMemcpyHostToDevice));
+  double2* hsd = reinterpret_cast<double2*>(ctx->k1d + 9 * Nmax);
+  PIC_CUDA_TRY(ctx, cudaMemcpy(hsd, hs.data(), 3 * Nmax * sizeof(double2), cudaMemcpyHostToDevice));
+  for (int a = 0; a < 3; ++a) {
+    ctx->ks[a] = ctx->k1d + (0 + a) * Nmax;
+    ctx->kc[a] = ctx->k1d + (3 + a) * Nmax;
+    ctx->zeta[a] = ctx->k1d + (6 + a) * Nmax;
+  }
+  // keep the half-cell shift tables right after the 1D tables
+  ctx->ncoef = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN ? COEF_COUNT : COEF_PSI1;
+  PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->coef, (size_t)ctx->ncoef * ctx->nmode * sizeof(double2)));
+  TableArgs t;
+  for (int a = 0; a < 3; ++a) {
+    t.ks[a] = ctx->ks[a];
+    t.kc[a] = ctx->kc[a];
+    t.vg[a] = ctx->variant == PIC_PSATD_STANDARD ? 0.0 : ctx->vg[a];
+  }
+  t.Ny = ctx->N[1];
+  t.nzh = ctx->nzh;
+  t.nmode = ctx->nmode;
+  t.dt = ctx->dt;
+  t.c = ctx->c;
+  t.eps0 = ctx->eps0;
+  t.ncoef = ctx->ncoef;
+  t.averaged = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN;
+  t.coef = ctx->coef;
+  gauss_legendre(&t.gl);
+  const int bs = 128;
+  build_tables_kernel<<<(unsigned)((ctx->nmode + bs - 1) / bs), bs, 0, ctx->stream>>>(t);
+  PIC_LAUNCH_CHECK(ctx);
+  PIC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return PIC_OK;
+}
+
+static const double2* half_shift(const pic_ctx* ctx, int a) {
+  const int64_t Nmax = std::max(ctx->N[0], std::max(ctx->N[1], ctx->N[2]));
+  return reinterpret_cast<const double2*>(ctx->k1d + 9 * Nmax) + a * Nmax;
+}
+
+pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
+                           int write_j) {
+  UpdArgs u;
+  u.EB = ctx->EBh;
+  u.J = ctx->Jh;
+  u.rn = rn;
+  u.rp = rp;
+  u.coef = ctx->coef;
+  u.G = ctx->G;
+  for (int a = 0; a < 3; ++a) {
+    u.ks[a] = ctx->ks[a];
+    u.zt[a] = ctx->zeta[a];
+    u.hs[a] = half_shift(ctx, a);
+  }
+  u.Ny = ctx->N[1];
+  u.nzh = ctx->nzh;
+  u.nmode = ctx->nmode;
+  u.c2 = ctx->c * ctx->c;
+  u.gscale = 1.0 / (double)ctx->ncell;
+  u.g_mode = g_mode;
+  u.j_yee = j_yee;
+  u.write_j = write_j;
+  const int bs = 256;
+  const unsigned nb = (unsigned)((ctx->nmode + bs - 1) / bs);
+  if (ctx->variant == PIC_PSATD_AVERAGED_GALILEAN)
+    update_kernel<2><<<nb, bs, 0, ctx->stream>>>(u);
+  else
+    update_kernel<0><<<nb, bs, 0, ctx->stream>>>(u);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
+
+pic_status psatd_update(pic_ctx* ctx, int cur) {
+  return psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], 0, 0, 1);
+}
+
+pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, int ncomp, int sign,
+                       double scale) {
+  PhaseArgs p;
+  p.in = in;
+  p.out = out;
+  for (int c = 0; c < ncomp; ++c) p.mask[c] = stag_mask(comp_kind[c]);
+  p.sign = sign;
+  p.scale = scale;
+  for (int a = 0; a < 3; ++a) p.hs[a] = half_shift(ctx, a);
+  p.Ny = ctx->N[1];
+  p.nzh = ctx->nzh;
+  p.nmode = ctx->nmode;
+  const int bs = 256;
+  dim3 grid((unsigned)((ctx->nmode + bs - 1) / bs), ncomp);
+  phase_kernel<<<grid, bs, 0, ctx->stream>>>(p);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
+
+pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale) {
+  NodalArgs a;
+  a.EB = EB6;
+  a.G = ctx->G;
+  for (int k = 0; k < 3; ++k) a.zt[k] = ctx->zeta[k];
+  a.Ny = ctx->N[1];
+  a.nzh = ctx->nzh;
+  a.nmode = ctx->nmode;
+  a.scale = scale;
+  const int bs = 256;
+  dim3 grid((unsigned)((ctx->nmode + bs - 1) / bs), 6);
+  to_nodal_kernel<<<grid, bs, 0, ctx->stream>>>(a);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libpic (include/pic.h): argument marshalling only.
+
+Every entry point of the C ABI has a same-named method on :class:`Context`
+(``pic_step`` -> ``Context.step`` ...).  Field and particle arguments are
+torch CUDA tensors (float64, contiguous); the binding passes their device
+pointers and the context's stream.  All computation happens in the CUDA
+library: if it cannot be loaded this module raises at import time.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+PIC_OK = 0
+STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_UNSUPPORTED", -3: "PIC_ERR_NOMEM",
+          -4: "PIC_ERR_CUDA", -5: "PIC_ERR_CAPACITY", -6: "PIC_ERR_TIMEOUT", -7: "PIC_ERR_NONFINITE"}
+STANDARD, GALILEAN, AVERAGED = 0, 1, 2
+
+_d3 = ctypes.c_double * 3
+_i3 = ctypes.c_int32 * 3
+_l3 = ctypes.c_int64 * 3
+_vp = ctypes.c_void_p
+
+
+class PicExt(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("spectral_order", _i3), ("precision", ctypes.c_int32),
+                ("c", ctypes.c_double), ("eps0", ctypes.c_double), ("tile", _i3),
+                ("sort_interval", ctypes.c_int32), ("cuda_stream", _vp)]
+
+
+class PicSpecies(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("q", ctypes.c_double), ("m", ctypes.c_double),
+                ("x", _vp), ("y", _vp), ("z", _vp), ("ux", _vp), ("uy", _vp), ("uz", _vp), ("w", _vp),
+                ("id", _vp)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libpic is not built (%s missing): run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    sig = {
+        "pic_ext_default": (None, [P(PicExt)]),
+        "pic_init": (ctypes.c_int, [P(_vp), P(ctypes.c_int64), P(ctypes.c_double), ctypes.c_double, ctypes.c_int,
+                                    P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_double), P(PicExt)]),
+        "pic_destroy": (None, [_vp]),
+        "pic_last_error": (ctypes.c_char_p, [_vp]),
+        "pic_sync": (ctypes.c_int, [_vp]),
+        "pic_step": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(_vp), _vp, P(PicSpecies), ctypes.c_int, ctypes.c_int]),
+        "pic_deposit_rho": (ctypes.c_int, [_vp, P(PicSpecies), ctypes.c_int, _vp]),
+        "pic_push_deposit": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(PicSpecies), ctypes.c_int, P(_vp), _vp]),
+        "pic_bin": (ctypes.c_int, [_vp, P(PicSpecies), _vp]),
+        "pic_num_tiles": (ctypes.c_int64, [_vp]),
+        "pic_center_to_nodal": (ctypes.c_int, [_vp, P(_vp), P(_vp)]),
+        "pic_center_to_yee": (ctypes.c_int, [_vp, P(_vp), P(_vp)]),
+        "pic_fft_forward": (ctypes.c_int, [_vp, P(_vp), P(_vp), ctypes.c_int]),
+        "pic_fft_inverse": (ctypes.c_int, [_vp, P(_vp), P(_vp), ctypes.c_int]),
+        "pic_maxwell_step": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(_vp), _vp, _vp, P(_vp), P(_vp)]),
+        "pic_coefficient": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
+        "pic_field_energy": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(ctypes.c_int64), P(ctypes.c_int64),
+                                            P(ctypes.c_double)]),
+        "pic_total_charge": (ctypes.c_int, [_vp, _vp, P(ctypes.c_double)]),
+        "pic_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "pic_timing_read": (ctypes.c_int, [_vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+EXPORTS = ("pic_ext_default", "pic_init", "pic_destroy", "pic_last_error", "pic_sync", "pic_step",
+           "pic_deposit_rho", "pic_push_deposit", "pic_bin", "pic_num_tiles", "pic_center_to_nodal",
+           "pic_center_to_yee", "pic_fft_forward", "pic_fft_inverse", "pic_maxwell_step",
+           "pic_coefficient", "pic_field_energy", "pic_total_charge", "pic_timing", "pic_timing_read")
+
+
+def _ptr(t, n=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype not in (torch.float64, torch.int64) or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float64/int64 tensor, got %s %s" % (t.device, t.dtype))
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, t.numel()))
+    return t.data_ptr()
+
+
+def _parr(ts, n=None):
+    arr = (_vp * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t, n)
+    return arr
+
+
+class Species:
+    """One particle species: torch CUDA float64 tensors x, y, z, ux, uy, uz, w (+ optional int64 id)."""
+
+    def __init__(self, x, y, z, ux, uy, uz, w, q, m, id=None):
+        self.x, self.y, self.z, self.ux, self.uy, self.uz, self.w = x, y, z, ux, uy, uz, w
+        self.q, self.m, self.id = float(q), float(m), id
+
+    @property
+    def n(self):
+        return self.x.numel()
+
+    def arrays(self):
+        return [self.x, self.y, self.z, self.ux, self.uy, self.uz, self.w]
+
+    def c_struct(self):
+        n = self.n
+        p = [_ptr(a, n) for a in self.arrays()]
+        return PicSpecies(n, self.q, self.m, *p, _ptr(self.id, n) if self.id is not None else None)
+
+
+def _species_array(species):
+    arr = (PicSpecies * max(1, len(species)))()
+    for i, s in enumerate(species):
+        arr[i] = s.c_struct()
+    return arr
+
+
+class Context:
+    """A libpic context (pic_init / pic_destroy) bound to a CUDA stream."""
+
+    def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
+                 v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0,
+                 tile=(8, 8, 8), sort_interval=20, stream=None):
+        self.shape = tuple(int(n) for n in shape)
+        self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
+        self.nmode = self.shape[0] * self.shape[1] * (self.shape[2] // 2 + 1)
+        self.variant = variant
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ext = PicExt()
+        LIB.pic_ext_default(ctypes.byref(ext))
+        ext.spectral_order = _i3(*spectral_order)
+        ext.c = c
+        ext.eps0 = eps0
+        ext.tile = _i3(*tile)
+        ext.sort_interval = sort_interval
+        ext.cuda_stream = self.stream.cuda_stream
+        h = _vp()
+        st = LIB.pic_init(ctypes.byref(h), _l3(*self.shape), _d3(*dx), dt, shape_order, _i3(*centering_order),
+                          variant, _d3(*v_gal), ctypes.byref(ext))
+        if st != PIC_OK:
+            raise PicError(st, "pic_init failed (see stderr)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            LIB.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != PIC_OK:
+            raise PicError(st, LIB.pic_last_error(self.h).decode())
+
+    def sync(self):
+        self._check(LIB.pic_sync(self.h))
+
+    def step(self, E, B, J, rho, species, nsteps):
+        """pic_step: E, B, J lists of 3 Yee arrays, rho nodal; species a list of Species."""
+        n = self.ncell
+        self._check(LIB.pic_step(self.h, _parr(E, n), _parr(B, n), _parr(J, n), _ptr(rho, n),
+                                 _species_array(species), len(species), nsteps))
+
+    def deposit_rho(self, species, rho):
+        self._check(LIB.pic_deposit_rho(self.h, _species_array(species), len(species), _ptr(rho, self.ncell)))
+
+    def push_deposit(self, En, Bn, species, Jn, rho):
+        n = self.ncell
+        self._check(LIB.pic_push_deposit(self.h, _parr(En, n), _parr(Bn, n), _species_array(species),
+                                         len(species), _parr(Jn, n), _ptr(rho, n)))
+
+    def num_tiles(self):
+        return int(LIB.pic_num_tiles(self.h))
+
+    def bin(self, species, offsets=None):
+        arr = _species_array([species])
+        self._check(LIB.pic_bin(self.h, arr, _ptr(offsets, self.num_tiles() + 1) if offsets is not None else None))
+
+    def center_to_nodal(self, F, out):
+        self._check(LIB.pic_center_to_nodal(self.h, _parr(F, self.ncell), _parr(out, self.ncell)))
+
+    def center_to_yee(self, Jn, out):
+        self._check(LIB.pic_center_to_yee(self.h, _parr(Jn, self.ncell), _parr(out, self.ncell)))
+
+    def fft_forward(self, real, spec):
+        self._check(LIB.pic_fft_forward(self.h, _parr(real, self.ncell), _parr(spec, 2 * self.nmode), len(real)))
+
+    def fft_inverse(self, spec, real):
+        self._check(LIB.pic_fft_inverse(self.h, _parr(spec, 2 * self.nmode), _parr(real, self.ncell), len(real)))
+
+    def maxwell_step(self, E, B, J, rho_n, rho_np1, Eavg=None, Bavg=None):
+        n = self.ncell
+        ea = _parr(Eavg, n) if Eavg is not None else None
+        ba = _parr(Bavg, n) if Bavg is not None else None
+        self._check(LIB.pic_maxwell_step(self.h, _parr(E, n), _parr(B, n), _parr(J, n), _ptr(rho_n, n),
+                                         _ptr(rho_np1, n), ea, ba))
+
+    def coefficient(self, name, out):
+        self._check(LIB.pic_coefficient(self.h, name.encode(), _ptr(out, 2 * self.nmode)))
+
+    def field_energy(self, E, B, box_lo=None, box_hi=None):
+        out = ctypes.c_double()
+        lo = _l3(*box_lo) if box_lo is not None else None
+        hi = _l3(*box_hi) if box_hi is not None else None
+        self._check(LIB.pic_field_energy(self.h, _parr(E, self.ncell), _parr(B, self.ncell), lo, hi,
+                                         ctypes.byref(out)))
+        return out.value
+
+    def total_charge(self, rho):
+        out = ctypes.c_double()
+        self._check(LIB.pic_total_charge(self.h, _ptr(rho, self.ncell), ctypes.byref(out)))
+        return out.value
+
+    def timing(self, enable):
+        self._check(LIB.pic_timing(self.h, 1 if enable else 0))
+
+    def timing_read(self, stage):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(LIB.pic_timing_read(self.h, stage.encode(), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value

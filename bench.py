@@ -286,7 +286,7 @@ def main():
         "roofline": roofline,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, _ = run_oracle_sample(args.workload, 1)
+        v, desc, _ = run_oracle_sample(args.workload, 4)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line), flush=True)

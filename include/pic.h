@@ -254,6 +254,35 @@ pic_status pic_field_energy(pic_ctx* ctx, const double* const E[3], const double
 pic_status pic_total_charge(pic_ctx* ctx, const double* rho, double* out);
 
 /*
+ * pic_center_to_nodal_static: the same centering as pic_center_to_nodal, for
+ * callers that cannot allocate device memory.  The paper has no counterpart;
+ * this exists for host programs that own every byte of device memory through
+ * their own pool and forbid other allocations, and for loops where the device
+ * synchronisation implied by cudaMalloc / cudaFree is not acceptable.  Such
+ * callers cannot create a pic_ctx (pic_init allocates), so this entry point
+ * takes the grid and orders directly and allocates nothing: it calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   grid[3]             Nx, Ny, Nz: powers of two in [2, 1024], with
+ *                       Nx * Ny * Nz <= 2,097,152 (2^21) cells, else PIC_ERR_CAPACITY.
+ *   centering_order[3]  as in pic_init.
+ *   F[6], out[6]        device arrays as in pic_center_to_nodal (caller-owned).
+ *   cuda_stream         a cudaStream_t, or NULL for the legacy default stream.
+ * Its scratch (the intermediate of the two-axis centering of B^x, B^y, B^z) is a
+ * file-scope static device array of 2^21 doubles (16 MiB) that every GPU which
+ * loads the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  All calls share the
+ * one array: calls that overlap on the GPU (different streams, or different host
+ * threads, without ordering between them) race on it.  Every element the
+ * scratch is read from is written first in the same call, so no clearing is
+ * needed.  Errors: PIC_ERR_ARG / PIC_ERR_UNSUPPORTED (bad arguments),
+ * PIC_ERR_CAPACITY (grid larger than the scratch; a message goes to stderr),
+ * PIC_ERR_CUDA (no current device or a failed launch).  Asynchronous.
+ */
+pic_status pic_center_to_nodal_static(const int64_t grid[3], const int32_t centering_order[3],
+                                      const double* const F[6], double* const out[6], void* cuda_stream);
+
+/*
  * pic_timing: enable (1) or disable (0) per-stage device timing and reset the
  * accumulators.  When enabled, each stage call of pic_step records a pair of
  * CUDA events on the context stream.  Stages: "push" (gather + Boris + deposit),

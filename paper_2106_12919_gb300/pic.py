@@ -70,6 +70,7 @@ def _load():
                                             P(ctypes.c_double)]),
         "pic_total_charge": (ctypes.c_int, [_vp, _vp, P(ctypes.c_double)]),
         "pic_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "pic_center_to_nodal_static": (ctypes.c_int, [P(ctypes.c_int64), P(ctypes.c_int32), P(_vp), P(_vp), _vp]),
         "pic_timing_read": (ctypes.c_int, [_vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
@@ -83,7 +84,8 @@ LIB = _load()
 EXPORTS = ("pic_ext_default", "pic_init", "pic_destroy", "pic_last_error", "pic_sync", "pic_step",
            "pic_deposit_rho", "pic_push_deposit", "pic_bin", "pic_num_tiles", "pic_center_to_nodal",
            "pic_center_to_yee", "pic_fft_forward", "pic_fft_inverse", "pic_maxwell_step",
-           "pic_coefficient", "pic_field_energy", "pic_total_charge", "pic_timing", "pic_timing_read")
+           "pic_coefficient", "pic_field_energy", "pic_total_charge", "pic_timing", "pic_timing_read",
+           "pic_center_to_nodal_static")
 
 
 def _ptr(t, n=None):
@@ -103,6 +105,18 @@ def _parr(ts, n=None):
     for i, t in enumerate(ts):
         arr[i] = _ptr(t, n)
     return arr
+
+
+def center_to_nodal_static(shape, centering_order, F, out, stream=None):
+    """pic_center_to_nodal_static: allocation-free Yee -> nodal centering (no context).
+
+    Returns the pic_status code (0 on success); raises nothing so that callers can
+    inspect PIC_ERR_CAPACITY for grids beyond the static scratch.
+    """
+    n = int(shape[0]) * int(shape[1]) * int(shape[2])
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return LIB.pic_center_to_nodal_static(_l3(*shape), _i3(*centering_order), _parr(F, n), _parr(out, n),
+                                          s.cuda_stream)
 
 
 class Species:

@@ -62,14 +62,17 @@ typedef enum {
   PIC_PSATD_AVERAGED_GALILEAN = 2  /* Sec. 4.4, Eqs. eq_update_B/E_with_rho_averaged */
 } pic_variant;
 
-typedef enum { PIC_FP64 = 0 } pic_precision;
+typedef enum {
+  PIC_FP64 = 0,  /* plain FP64 form: every array double, FP64 arithmetic */
+  PIC_FP32 = 1   /* FP32 form: FP32 fields, particles and FFTs; FP64 coefficient tables and diagnostics */
+} pic_precision;
 
 /*
  * Optional extension block (pass NULL for defaults).  struct_size must be
  * sizeof(pic_ext) of the caller's header (versioning).
  *   spectral_order[3]: order 2m of the modified wave numbers [k]_s, [k]_c of
  *     Sec. 4.1 per axis; 0 = infinite order ([k] = k).  Default 0.
- *   precision: PIC_FP64 (only value accepted).
+ *   precision: PIC_FP64 (the pic_step family) or PIC_FP32 (the pic_step32 family).
  *   c, eps0: speed of light and vacuum permittivity.  Defaults 1, 1.
  *   tile[3]: particle tile edge in cells per axis for binning (powers of two
  *     dividing the grid).  Default 8, 8, 8.
@@ -252,6 +255,62 @@ pic_status pic_field_energy(pic_ctx* ctx, const double* const E[3], const double
 
 /* pic_total_charge: sum(rho) dV of a nodal array; *out is a HOST double.  Synchronous. */
 pic_status pic_total_charge(pic_ctx* ctx, const double* rho, double* out);
+
+/*
+ * ---------------------------------------------------------------------------
+ * FP32 form (contexts created with precision = PIC_FP32).  Same step, same
+ * readings of the paper; fields, particles, deposits and FFTs in FP32; the PSATD
+ * coefficient tables stay FP64 (rounded to FP32 at use) and the energy / charge
+ * reductions accumulate in FP64.  Calling an FP32 entry point on an FP64
+ * context (or the reverse) returns PIC_ERR_ARG.
+ * ---------------------------------------------------------------------------
+ *
+ * One species in the FP32 form, device SoA of n particles.
+ *   cell       int32 linear index (ix * Ny + iy) * Nz + iz of the cell holding
+ *              the particle (node (ix, iy, iz) is its lower corner).
+ *   fx, fy, fz FP32 offsets in [0, 1) inside that cell, in units of the cell size:
+ *              position x = (ix + fx) dx, etc.
+ *   ux, uy, uz, w, id, q, m: as in pic_species (FP32 arrays; id optional).
+ * Arrays may be permuted in place by binning, as in the FP64 form.
+ */
+typedef struct {
+  int64_t n;
+  double q;
+  double m;
+  int32_t* cell;
+  float* fx;
+  float* fy;
+  float* fz;
+  float* ux;
+  float* uy;
+  float* uz;
+  float* w;
+  int64_t* id;
+} pic_species32;
+
+/* pic_step32: pic_step in the FP32 form; E, B, J (Yee) and rho (nodal) are float arrays. */
+pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float* const J[3], float* rho,
+                      const pic_species32* sp, int n_species, int nsteps);
+
+/* pic_deposit_rho32: pic_deposit_rho in the FP32 form. */
+pic_status pic_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, int n_species, float* rho);
+
+/* pic_push_deposit32: pic_push_deposit in the FP32 form (nodal float fields in, nodal float J, rho out). */
+pic_status pic_push_deposit32(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
+                              const pic_species32* sp, int n_species, float* const J_nodal[3], float* rho_nodal);
+
+/* pic_bin32: pic_bin in the FP32 form (tile from the integer cell index). */
+pic_status pic_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets);
+
+/* pic_fft_forward32 / pic_fft_inverse32: pic_fft_forward / inverse on float arrays
+ * (spectra: Nx*Ny*(Nz/2+1) (re, im) float pairs). */
+pic_status pic_fft_forward32(pic_ctx* ctx, const float* const real[], float* const spec[], int ncomp);
+pic_status pic_fft_inverse32(pic_ctx* ctx, float* const spec[], float* const real[], int ncomp);
+
+/* pic_field_energy32 / pic_total_charge32: FP64 reductions over float arrays (HOST results). */
+pic_status pic_field_energy32(pic_ctx* ctx, const float* const E[3], const float* const B[3],
+                              const int64_t box_lo[3], const int64_t box_hi[3], double* out);
+pic_status pic_total_charge32(pic_ctx* ctx, const float* rho, double* out);
 
 /*
  * pic_center_to_nodal_static: the same centering as pic_center_to_nodal, for

@@ -176,7 +176,7 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   if (!(dt > 0.0)) return fail(PIC_ERR_ARG, "dt must be > 0");
   if (shape_order < 1 || shape_order > 3) return fail(PIC_ERR_ARG, "shape order must be 1, 2 or 3");
   if (psatd_variant < 0 || psatd_variant > 2) return fail(PIC_ERR_ARG, "unknown PSATD variant");
-  if (e.precision != PIC_FP64) return fail(PIC_ERR_UNSUPPORTED, "only PIC_FP64 is available");
+  if (e.precision != PIC_FP64 && e.precision != PIC_FP32) return fail(PIC_ERR_ARG, "precision must be PIC_FP64 or PIC_FP32");
   if (!(e.c > 0.0) || !(e.eps0 > 0.0)) return fail(PIC_ERR_ARG, "c and eps0 must be > 0");
   if (psatd_variant != PIC_PSATD_STANDARD) {
     if (!v_gal) return fail(PIC_ERR_ARG, "v_gal required");
@@ -197,6 +197,7 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   ctx->c = e.c;
   ctx->eps0 = e.eps0;
   ctx->sort_interval = e.sort_interval;
+  ctx->precision = e.precision;
   ctx->stream = reinterpret_cast<cudaStream_t>(e.cuda_stream);
   ctx->ncell = grid[0] * grid[1] * grid[2];
   ctx->nzh = grid[2] / 2 + 1;
@@ -235,6 +236,7 @@ int64_t pic_num_tiles(const pic_ctx* ctx) { return ctx ? ctx->n_tiles : -1; }
 
 pic_status pic_deposit_rho(pic_ctx* ctx, const pic_species* sp, int n_species, double* rho) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!rho) return pic_set_error(ctx, PIC_ERR_ARG, "rho is null");
   PIC_TRY(check_species(ctx, sp, n_species));
   PIC_CUDA_TRY(ctx, cudaMemsetAsync(rho, 0, ctx->ncell * sizeof(double), ctx->stream));
@@ -245,6 +247,7 @@ pic_status pic_deposit_rho(pic_ctx* ctx, const pic_species* sp, int n_species, d
 pic_status pic_push_deposit(pic_ctx* ctx, const double* const En[3], const double* const Bn[3],
                             const pic_species* sp, int n_species, double* const J_nodal[3], double* rho_nodal) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(En, 3) || !all_nonnull(Bn, 3) || !all_nonnull(J_nodal, 3) || !rho_nodal)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   PIC_TRY(check_species(ctx, sp, n_species));
@@ -257,24 +260,28 @@ pic_status pic_push_deposit(pic_ctx* ctx, const double* const En[3], const doubl
 
 pic_status pic_bin(pic_ctx* ctx, const pic_species* sp, int64_t* offsets) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   PIC_TRY(check_species(ctx, sp, 1));
   return particles_bin(ctx, sp, offsets);
 }
 
 pic_status pic_center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(F, 6) || !all_nonnull(out, 6)) return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   return center_to_nodal(ctx, F, out);
 }
 
 pic_status pic_center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* const out[3]) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(Jn, 3) || !all_nonnull(out, 3)) return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   return center_to_yee(ctx, Jn, out);
 }
 
 pic_status pic_fft_forward(pic_ctx* ctx, const double* const real[], double* const spec[], int ncomp) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (ncomp < 1 || ncomp > 6 || !all_nonnull(real, ncomp) || !all_nonnull(spec, ncomp))
     return pic_set_error(ctx, PIC_ERR_ARG, "fft arguments");
   CRPtr6 in;
@@ -288,6 +295,7 @@ pic_status pic_fft_forward(pic_ctx* ctx, const double* const real[], double* con
 
 pic_status pic_fft_inverse(pic_ctx* ctx, double* const spec[], double* const real[], int ncomp) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (ncomp < 1 || ncomp > 6 || !all_nonnull(real, ncomp) || !all_nonnull(spec, ncomp))
     return pic_set_error(ctx, PIC_ERR_ARG, "fft arguments");
   CPtr6 in;
@@ -303,6 +311,7 @@ pic_status pic_maxwell_step(pic_ctx* ctx, double* const E[3], double* const B[3]
                             const double* rho_n, const double* rho_np1, double* const Eavg[3],
                             double* const Bavg[3]) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || !all_nonnull(J, 3) || !rho_n || !rho_np1)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   const bool avg = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN;
@@ -360,6 +369,7 @@ pic_status pic_coefficient(pic_ctx* ctx, const char* name, double* out) {
 pic_status pic_field_energy(pic_ctx* ctx, const double* const E[3], const double* const B[3],
                             const int64_t box_lo[3], const int64_t box_hi[3], double* out) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || !out) return pic_set_error(ctx, PIC_ERR_ARG, "null argument");
   int64_t lo[3] = {0, 0, 0}, hi[3] = {ctx->N[0], ctx->N[1], ctx->N[2]};
   if (box_lo && box_hi)
@@ -374,6 +384,7 @@ pic_status pic_field_energy(pic_ctx* ctx, const double* const E[3], const double
 
 pic_status pic_total_charge(pic_ctx* ctx, const double* rho, double* out) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!rho || !out) return pic_set_error(ctx, PIC_ERR_ARG, "null argument");
   PIC_TRY(diag_sum(ctx, rho, out));
   *out *= ctx->dx[0] * ctx->dx[1] * ctx->dx[2];
@@ -383,6 +394,7 @@ pic_status pic_total_charge(pic_ctx* ctx, const double* rho, double* out) {
 pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double* const J[3], double* rho,
                     const pic_species* sp, int n_species, int nsteps) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || !all_nonnull(J, 3) || !rho)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   if (nsteps < 0) return pic_set_error(ctx, PIC_ERR_ARG, "nsteps < 0");

@@ -1,4 +1,5 @@
-// 3D real-to-complex FFT for the PSATD solver: shared-memory Stockham kernels.
+// 3D real-to-complex FFT for the PSATD solver: shared-memory Stockham kernels,
+// templated on the precision (FP64 form: double; FP32 form: float).
 //
 // Forward: z-axis R2C (a length-Nz/2 complex FFT of packed (even, odd) pairs
 // followed by the split step), then in-place C2C along y and along x.
@@ -11,7 +12,7 @@
 // z lines are contiguous (line-major tile, padded one slot per 8 elements to
 // keep the radix-8 scatter conflict-free); y and x lines are strided, so a CTA
 // takes W adjacent columns (consecutive k_z) and the tile is element-major,
-// which keeps the global loads coalesced in W * 16-byte rows.
+// which keeps the global loads coalesced in W-element rows.
 #include "pic_internal.cuh"
 
 #include <cmath>
@@ -40,44 +41,48 @@ struct LayCol {  // y / x pass: element e of column w at e * W + w
 };
 
 // multiply by -i (forward) or +i (inverse)
-template <bool INV>
-__device__ __forceinline__ double2 rot90(double2 a) {
-  return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+template <bool INV, class C>
+__device__ __forceinline__ C rot90(C a) {
+  C r;
+  if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft4(double2& y0, double2& y1, double2& y2, double2& y3) {
-  double2 t0 = cadd(y0, y2), t1 = csub(y0, y2);
-  double2 t2 = cadd(y1, y3), t3 = rot90<INV>(csub(y1, y3));
+template <bool INV, class C>
+__device__ __forceinline__ void dft4(C& y0, C& y1, C& y2, C& y3) {
+  C t0 = cadd(y0, y2), t1 = csub(y0, y2);
+  C t2 = cadd(y1, y3), t3 = rot90<INV>(csub(y1, y3));
   y0 = cadd(t0, t2);
   y2 = csub(t0, t2);
   y1 = cadd(t1, t3);
   y3 = csub(t1, t3);
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void dft(double2* v) {
+template <int R, bool INV, class C>
+__device__ __forceinline__ void dft(C* v) {
+  using T = decltype(v[0].x);
   if (R == 2) {
-    double2 a = v[0];
+    C a = v[0];
     v[0] = cadd(a, v[1]);
     v[1] = csub(a, v[1]);
   } else if (R == 4) {
     dft4<INV>(v[0], v[1], v[2], v[3]);
   } else {  // R == 8: radix-2 split over n and n+4, then two radix-4 DFTs
-    const double r2 = 0.70710678118654752440;
-    double2 b[4], c[4];
+    const T r2 = (T)0.70710678118654752440;
+    C b[4], c[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
       b[n] = cadd(v[n], v[n + 4]);
       c[n] = csub(v[n], v[n + 4]);
     }
     // c_n *= w8^n, w8 = exp(-+ 2 pi i / 8)
+    C c1 = c[1], c3 = c[3];
     if (INV) {
-      c[1] = make_double2((c[1].x - c[1].y) * r2, (c[1].x + c[1].y) * r2);
-      c[3] = make_double2((-c[3].x - c[3].y) * r2, (c[3].x - c[3].y) * r2);
+      c[1].x = (c1.x - c1.y) * r2; c[1].y = (c1.x + c1.y) * r2;
+      c[3].x = (-c3.x - c3.y) * r2; c[3].y = (c3.x - c3.y) * r2;
     } else {
-      c[1] = make_double2((c[1].x + c[1].y) * r2, (c[1].y - c[1].x) * r2);
-      c[3] = make_double2((c[3].y - c[3].x) * r2, (-c[3].x - c[3].y) * r2);
+      c[1].x = (c1.x + c1.y) * r2; c[1].y = (c1.y - c1.x) * r2;
+      c[3].x = (c3.y - c3.x) * r2; c[3].y = (-c3.x - c3.y) * r2;
     }
     c[2] = rot90<INV>(c[2]);
     dft4<INV>(b[0], b[1], b[2], b[3]);
@@ -92,13 +97,13 @@ __device__ __forceinline__ void dft(double2* v) {
 
 // One Stockham pass of radix R on all lines of the tile, in place.  The CTA has
 // exactly L * N / 8 threads; each thread handles 8 / R butterflies.
-template <int R, bool INV, class LAY>
-__device__ __forceinline__ void stockham_pass(double2* s, const LAY& lay, int N, int Ns,
-                                              const double2* __restrict__ tw, int twstride) {
+template <int R, bool INV, class C, class LAY>
+__device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int N, int Ns, const C* __restrict__ tw,
+                                              int twstride) {
   constexpr int PER = 8 / R;
   const int T = blockDim.x;
   const int nb = N / R;
-  double2 v[PER][R];
+  C v[PER][R];
   int ol[PER], oj[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -119,7 +124,7 @@ __device__ __forceinline__ void stockham_pass(double2* s, const LAY& lay, int N,
       const int step = (N / (Ns * R)) * k;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        double2 w = __ldg(&tw[step * r * twstride]);
+        C w = __ldg(&tw[step * r * twstride]);
         if (INV) w.y = -w.y;
         v[q][r] = cmul(v[q][r], w);
       }
@@ -132,8 +137,8 @@ __device__ __forceinline__ void stockham_pass(double2* s, const LAY& lay, int N,
   __syncthreads();
 }
 
-template <bool INV, class LAY>
-__device__ void fft_tile(double2* s, const LAY& lay, int N, const double2* __restrict__ tw, int twstride) {
+template <bool INV, class C, class LAY>
+__device__ void fft_tile(C* s, const LAY& lay, int N, const C* __restrict__ tw, int twstride) {
   int Ns = 1, rem = N;
   while (rem >= 8) {
     stockham_pass<8, INV>(s, lay, N, Ns, tw, twstride);
@@ -145,71 +150,86 @@ __device__ void fft_tile(double2* s, const LAY& lay, int N, const double2* __res
 }
 
 // z-axis real-to-complex: L lines of Nz reals -> Nz/2+1 complex per line.
-__global__ void __launch_bounds__(kMaxThreads) fft_z_r2c_kernel(CRPtr6 in, CPtr6 out, int Nz, int64_t nlines,
-                                                               int L, const double2* __restrict__ tw) {
-  extern __shared__ double2 sm[];
+template <class T>
+__global__ void __launch_bounds__(kMaxThreads) fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int Nz,
+                                                               int64_t nlines, int L,
+                                                               const typename Cplx<T>::type* __restrict__ tw) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
   const int M = Nz / 2;
   const LayLine lay{M + M / 8};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
-  const double2* src = reinterpret_cast<const double2*>(in.p[comp]);
+  const C* src = reinterpret_cast<const C*>(in.p[comp]);
   for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
     const int l = t / M, e = t - l * M;
     const int64_t line = line0 + l;
-    sm[lay.idx(e, l)] = line < nlines ? src[line * M + e] : make_double2(0.0, 0.0);
+    sm[lay.idx(e, l)] = line < nlines ? src[line * M + e] : czero<C>();
   }
   __syncthreads();
   fft_tile<false>(sm, lay, M, tw, 2);
   // split: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W^k (Z_k - conj Z_{M-k}),  W = exp(-2 pi i / Nz)
-  double2* dst = out.p[comp];
+  C* dst = out.p[comp];
   const int nzh = M + 1, P = M / 2 + 1;
+  const T h = (T)0.5;
   for (int t = threadIdx.x; t < L * P; t += blockDim.x) {
     const int l = t / P, k = t - l * P;
     const int64_t line = line0 + l;
     if (line >= nlines) continue;
-    const double2 Zk = sm[lay.idx(k, l)];
-    const double2 Zm = sm[lay.idx((M - k) & (M - 1), l)];
-    const double2 Fe = make_double2(0.5 * (Zk.x + Zm.x), 0.5 * (Zk.y - Zm.y));
-    const double2 Fo = make_double2(0.5 * (Zk.y + Zm.y), -0.5 * (Zk.x - Zm.x));
-    const double2 wFo = cmul(__ldg(&tw[k]), Fo);
-    double2* o = dst + line * nzh;
+    const C Zk = sm[lay.idx(k, l)];
+    const C Zm = sm[lay.idx((M - k) & (M - 1), l)];
+    C Fe, Fo;
+    Fe.x = h * (Zk.x + Zm.x);
+    Fe.y = h * (Zk.y - Zm.y);
+    Fo.x = h * (Zk.y + Zm.y);
+    Fo.y = -h * (Zk.x - Zm.x);
+    const C wFo = cmul(__ldg(&tw[k]), Fo);
+    C* o = dst + line * nzh;
     o[k] = cadd(Fe, wFo);
     if (k != M - k) o[M - k] = cconj(csub(Fe, wFo));
   }
 }
 
 // z-axis complex-to-real (unnormalised inverse); the imaginary parts of X_0, X_{Nz/2} are ignored.
-__global__ void __launch_bounds__(kMaxThreads) fft_z_c2r_kernel(CPtr6 in, RPtr6 out, int Nz, int64_t nlines,
-                                                               int L, const double2* __restrict__ tw) {
-  extern __shared__ double2 sm[];
+template <class T>
+__global__ void __launch_bounds__(kMaxThreads) fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int Nz,
+                                                               int64_t nlines, int L,
+                                                               const typename Cplx<T>::type* __restrict__ tw) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
   const int M = Nz / 2;
   const LayLine lay{M + M / 8};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
-  const double2* srcb = in.p[comp];
+  const C* srcb = in.p[comp];
   const int nzh = M + 1, P = M / 2 + 1;
   // Z_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
   for (int t = threadIdx.x; t < L * P; t += blockDim.x) {
     const int l = t / P, k = t - l * P;
     const int64_t line = line0 + l;
-    double2 Xk = make_double2(0.0, 0.0), Xm = make_double2(0.0, 0.0);
+    C Xk = czero<C>(), Xm = czero<C>();
     if (line < nlines) {
       Xk = srcb[line * nzh + k];
       Xm = srcb[line * nzh + (M - k)];
     }
     if (k == 0) {
-      Xk.y = 0.0;
-      Xm.y = 0.0;
+      Xk.y = 0;
+      Xm.y = 0;
     }
-    const double2 A = make_double2(Xk.x + Xm.x, Xk.y - Xm.y);
-    const double2 D = make_double2(Xk.x - Xm.x, Xk.y + Xm.y);
-    const double2 w = __ldg(&tw[k]);
+    C A, D;
+    A.x = Xk.x + Xm.x;
+    A.y = Xk.y - Xm.y;
+    D.x = Xk.x - Xm.x;
+    D.y = Xk.y + Xm.y;
+    const C w = __ldg(&tw[k]);
     sm[lay.idx(k, l)] = cadd(A, cmuli(cmul(cconj(w), D)));
     if (k != 0 && k != M - k) sm[lay.idx(M - k, l)] = cadd(cconj(A), cmuli(cmul(w, cconj(D))));
   }
   __syncthreads();
   fft_tile<true>(sm, lay, M, tw, 2);
-  double2* dst = reinterpret_cast<double2*>(out.p[comp]);
+  C* dst = reinterpret_cast<C*>(out.p[comp]);
   for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
     const int l = t / M, e = t - l * M;
     const int64_t line = line0 + l;
@@ -219,18 +239,19 @@ __global__ void __launch_bounds__(kMaxThreads) fft_z_c2r_kernel(CPtr6 in, RPtr6 
 
 // In-place C2C along a strided axis: element e of column col of outer line o of
 // component c at p[c] + o * os + e * es + col.  A CTA takes W adjacent columns.
-template <bool INV>
-__global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CPtr6 data, int N, int64_t es, int64_t os,
-                                                                 int ncols, int W, const double2* __restrict__ tw) {
-  extern __shared__ double2 sm[];
+template <bool INV, class C>
+__global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CP6<C> data, int N, int64_t es, int64_t os,
+                                                                 int ncols, int W, const C* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
   const LayCol lay{W};
   const int comp = blockIdx.z;
   const int col0 = blockIdx.x * W;
-  double2* base = data.p[comp] + (int64_t)blockIdx.y * os + col0;
+  C* base = data.p[comp] + (int64_t)blockIdx.y * os + col0;
   const int wv = min(W, ncols - col0);
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     const int e = t / W, w = t - e * W;
-    sm[t] = w < wv ? base[e * es + w] : make_double2(0.0, 0.0);
+    sm[t] = w < wv ? base[e * es + w] : czero<C>();
   }
   __syncthreads();
   fft_tile<INV>(sm, lay, N, tw, 1);
@@ -242,7 +263,12 @@ __global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CPtr6 data, in
 
 int strided_width(int N) { return N >= 1024 ? 8 : 16; }
 
-pic_status launch_strided(pic_ctx* ctx, CPtr6 d, int axis, bool inv, int ncomp) {
+template <class C> const C* twiddles(const pic_ctx* ctx, int a);
+template <> const double2* twiddles<double2>(const pic_ctx* ctx, int a) { return ctx->twid[a]; }
+template <> const float2* twiddles<float2>(const pic_ctx* ctx, int a) { return ctx->twid32[a]; }
+
+template <class C>
+pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp) {
   const int N = (int)ctx->N[axis];
   const int W = strided_width(N);
   const int nzh = (int)ctx->nzh;
@@ -258,16 +284,28 @@ pic_status launch_strided(pic_ctx* ctx, CPtr6 d, int axis, bool inv, int ncomp) 
   }
   dim3 grid((nzh + W - 1) / W, (unsigned)nouter, ncomp);
   const int threads = W * N / 8;
-  const size_t smem = (size_t)W * N * sizeof(double2);
+  const size_t smem = (size_t)W * N * sizeof(C);
   if (inv)
-    fft_strided_kernel<true><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, ctx->twid[axis]);
+    fft_strided_kernel<true, C><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, twiddles<C>(ctx, axis));
   else
-    fft_strided_kernel<false><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, ctx->twid[axis]);
+    fft_strided_kernel<false, C><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, twiddles<C>(ctx, axis));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
 
 int z_lines_per_cta(int Nz) { return kZTile / (Nz / 2); }
+
+template <class T>
+pic_status set_smem_attrs(pic_ctx* ctx) {
+  using C = typename Cplx<T>::type;
+  const int zsm = kZTile * 9 / 8 * (int)sizeof(C);
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
+  const int ssm = 8192 * (int)sizeof(C);
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<false, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<true, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  return PIC_OK;
+}
 
 }  // namespace
 
@@ -292,49 +330,59 @@ pic_status fft_setup(pic_ctx* ctx) {
   for (int a = 0; a < 3; ++a) {
     const int64_t N = ctx->N[a];
     double2* h = new double2[N];
+    float2* hf = new float2[N];
     for (int64_t j = 0; j < N; ++j) {
       double s, c;
       sincospi_frac(2 * j, N, &s, &c);
       h[j] = make_double2(c, -s);  // exp(-2 pi i j / N)
+      hf[j] = make_float2((float)c, (float)-s);
     }
     cudaError_t e = cudaMalloc(&ctx->twid[a], N * sizeof(double2));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->twid[a], h, N * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->twid32[a], N * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twid32[a], hf, N * sizeof(float2), cudaMemcpyHostToDevice);
     delete[] h;
+    delete[] hf;
     if (e != cudaSuccess) return pic_set_error(ctx, PIC_ERR_NOMEM, "twiddle table: %s", cudaGetErrorString(e));
   }
-  const int zsm = kZTile * 9 / 8 * (int)sizeof(double2);
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_r2c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_c2r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
-  const int ssm = 8192 * (int)sizeof(double2);
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
-  return PIC_OK;
+  pic_status st = set_smem_attrs<double>(ctx);
+  if (st != PIC_OK) return st;
+  return set_smem_attrs<float>(ctx);
 }
 
-pic_status fft_r2c(pic_ctx* ctx, CRPtr6 in, CPtr6 out, int ncomp) {
+template <class T>
+pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp) {
+  using C = typename Cplx<T>::type;
   const int Nz = (int)ctx->N[2];
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
-  const size_t smem = (size_t)L * (Nz / 2 + Nz / 16) * sizeof(double2);
-  fft_z_r2c_kernel<<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, ctx->twid[2]);
+  const size_t smem = (size_t)L * (Nz / 2 + Nz / 16) * sizeof(C);
+  fft_z_r2c_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
-  pic_status st = launch_strided(ctx, out, 1, false, ncomp);
+  pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
   if (st != PIC_OK) return st;
-  return launch_strided(ctx, out, 0, false, ncomp);
+  return launch_strided<C>(ctx, out, 0, false, ncomp);
 }
 
-pic_status fft_c2r(pic_ctx* ctx, CPtr6 in, RPtr6 out, int ncomp) {
-  pic_status st = launch_strided(ctx, in, 0, true, ncomp);
+template <class T>
+pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp) {
+  using C = typename Cplx<T>::type;
+  pic_status st = launch_strided<C>(ctx, in, 0, true, ncomp);
   if (st != PIC_OK) return st;
-  st = launch_strided(ctx, in, 1, true, ncomp);
+  st = launch_strided<C>(ctx, in, 1, true, ncomp);
   if (st != PIC_OK) return st;
   const int Nz = (int)ctx->N[2];
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
-  const size_t smem = (size_t)L * (Nz / 2 + Nz / 16) * sizeof(double2);
-  fft_z_c2r_kernel<<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, ctx->twid[2]);
+  const size_t smem = (size_t)L * (Nz / 2 + Nz / 16) * sizeof(C);
+  fft_z_c2r_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
+
+template pic_status fft_r2c<double>(pic_ctx*, CRP6<double>, CP6<double2>, int);
+template pic_status fft_r2c<float>(pic_ctx*, CRP6<float>, CP6<float2>, int);
+template pic_status fft_c2r<double>(pic_ctx*, CP6<double2>, RP6<double>, int);
+template pic_status fft_c2r<float>(pic_ctx*, CP6<float2>, RP6<float>, int);

@@ -324,6 +324,8 @@ int ilog2(int v) {
 
 }  // namespace
 
+pic_status particles_bin_capacity(pic_ctx* ctx, int64_t n) { return ensure_bin_capacity(ctx, n); }
+
 pic_status particles_push(pic_ctx* ctx, const double* const En[3], const double* const Bn[3],
                           const pic_species* sp, double* const J[3], double* rho) {
   PushArgs a = make_args(ctx, sp);

@@ -28,6 +28,24 @@ __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }
+
+// Scalar / complex type pair of a precision: Real<double>::C = double2, Real<float>::C = float2.
+template <class T> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+__host__ __device__ __forceinline__ double2 to_c(double2 v, double2*) { return v; }
+__host__ __device__ __forceinline__ float2 to_c(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
+template <class C> __host__ __device__ __forceinline__ C cast_c(double2 v) { return to_c(v, (C*)nullptr); }
+template <class C> __host__ __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
+
 // Index of a coefficient table inside pic_ctx::coef.
 enum CoefIdx {
   COEF_TC = 0, COEF_TS, COEF_X1, COEF_X2, COEF_TX3, COEF_X4,
@@ -64,6 +82,7 @@ struct pic_ctx {
   double c, eps0;
   int tile[3];
   int sort_interval;
+  int precision;
   cudaStream_t stream;
   int64_t ncell, nzh, nmode;
   int ncoef;
@@ -75,6 +94,7 @@ struct pic_ctx {
   double* kc[3];
   double* zeta[3];
   double2* twid[3];  // twiddles exp(-2 pi i j / N_a), j < N_a
+  float2* twid32[3]; // the same rounded to FP32
   double2* coef;     // [ncoef][nmode]
 
   // spectral state and work (paper-convention spectra)
@@ -128,17 +148,22 @@ pic_status pic_set_error(pic_ctx* ctx, pic_status st, const char* fmt, ...);
                            cudaGetErrorString(e_));                                  \
   } while (0)
 
-// Real-space component pointer bundles passed by value to kernels.
-struct RPtr6 { double* p[6]; };
-struct CRPtr6 { const double* p[6]; };
-struct CPtr6 { double2* p[6]; };
+// Component pointer bundles passed by value to kernels.
+template <class T> struct RP6 { T* p[6]; };
+template <class T> struct CRP6 { const T* p[6]; };
+template <class C> struct CP6 { C* p[6]; };
+using RPtr6 = RP6<double>;
+using CRPtr6 = CRP6<double>;
+using CPtr6 = CP6<double2>;
 
 // fft.cu ---------------------------------------------------------------------
 pic_status fft_setup(pic_ctx* ctx);
-// Forward R2C of ncomp real arrays into spectral arrays (plain DFT, unnormalised).
-pic_status fft_r2c(pic_ctx* ctx, CRPtr6 in, CPtr6 out, int ncomp);
+// Forward R2C of ncomp real arrays into spectral arrays (plain DFT, unnormalised). T = double | float.
+template <class T>
+pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp);
 // Inverse C2R (unnormalised); spectral arrays are destroyed.
-pic_status fft_c2r(pic_ctx* ctx, CPtr6 in, RPtr6 out, int ncomp);
+template <class T>
+pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp);
 
 // psatd.cu -------------------------------------------------------------------
 pic_status psatd_setup(pic_ctx* ctx);   // 1D tables + per-mode coefficient tables
@@ -156,12 +181,24 @@ pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, 
                        double scale);
 // G[c] = Z_c * src[c] * scale, src = the six E,B spectra given (paper convention) -> nodal DFT.
 pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale);
+// FP32-form counterparts (FP32 spectra, FP64 tables rounded at use).
+pic_status psatd_update32(pic_ctx* ctx, float2* EB, float2* J, const float2* rn, const float2* rp, float2* G,
+                          int g_mode, int j_yee, int write_j);
+pic_status psatd_phase32(pic_ctx* ctx, CP6<float2> in, CP6<float2> out, const int* comp_kind, int ncomp, int sign,
+                         double scale);
+pic_status psatd_to_nodal32(pic_ctx* ctx, const float2* EB6, float2* G, double scale);
 
 // particles.cu ----------------------------------------------------------------
 pic_status particles_push(pic_ctx* ctx, const double* const En[3], const double* const Bn[3],
                           const pic_species* sp, double* const J[3], double* rho);
 pic_status particles_deposit_rho(pic_ctx* ctx, const pic_species* sp, double* rho);
 pic_status particles_bin(pic_ctx* ctx, const pic_species* sp, int64_t* offsets_out);
+pic_status particles_bin_capacity(pic_ctx* ctx, int64_t n);
+// FP32 form (particles32.cu)
+pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
+                            const pic_species32* sp, float* const J[3], float* rho);
+pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float* rho);
+pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out);
 
 // center.cu -------------------------------------------------------------------
 pic_status center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);
@@ -171,6 +208,9 @@ pic_status center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* const 
 pic_status diag_energy(pic_ctx* ctx, const double* const E[3], const double* const B[3],
                        const int64_t lo[3], const int64_t hi[3], double* out);
 pic_status diag_sum(pic_ctx* ctx, const double* a, double* out);
+pic_status diag_energy32(pic_ctx* ctx, const float* const E[3], const float* const B[3],
+                         const int64_t lo[3], const int64_t hi[3], double* out);
+pic_status diag_sum32(pic_ctx* ctx, const float* a, double* out);
 
 // Exact-reduction sin/cos of pi * p / q for integers (host), used to build tables.
 void sincospi_frac(int64_t p, int64_t q, double* s, double* c);

@@ -237,13 +237,14 @@ __global__ void build_tables_kernel(TableArgs t) {
 // ---------------------------------------------------------------------------
 // fused update
 // ---------------------------------------------------------------------------
+template <class C>
 struct UpdArgs {
-  double2* EB;          // [6][nmode] in/out
-  double2* J;           // [3][nmode] in: DFT of the nodal (or Yee, j_yee) deposit; out: Yee-centered
-  const double2* rn;    // rho^n
-  const double2* rp;    // rho^{n+1}
-  const double2* coef;  // [ncoef][nmode]
-  double2* G;           // [6][nmode] out
+  C* EB;                // [6][nmode] in/out
+  C* J;                 // [3][nmode] in: DFT of the nodal (or Yee, j_yee) deposit; out: Yee-centered
+  const C* rn;          // rho^n
+  const C* rp;          // rho^{n+1}
+  const double2* coef;  // [ncoef][nmode], FP64 in every form
+  C* G;                 // [6][nmode] out
   const double* ks[3];
   const double* zt[3];
   const double2* hs[3];  // half-cell shifts exp(-i k dx / 2)
@@ -255,18 +256,19 @@ struct UpdArgs {
   int write_j;  // write the Yee-centered J back
 };
 
-__device__ __forceinline__ double2 ld(const double2* p) { return __ldg(p); }
-
-template <int VAR>
-__global__ void __launch_bounds__(256) update_kernel(UpdArgs u) {
+// Fused k-space update of one mode per thread.  The FP64 coefficient tables are
+// read in FP64 and rounded to the data precision at use.
+template <int VAR, class C>
+__global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
+  using T = decltype(C().x);
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= u.nmode) return;
   const int64_t nm = u.nmode;
   const int64_t iz = m % u.nzh, r = m / u.nzh;
   const int64_t iy = r % u.Ny, ix = r / u.Ny;
-  const double k[3] = {u.ks[0][ix], u.ks[1][iy], u.ks[2][iz]};
-  const double zx = u.zt[0][ix], zy = u.zt[1][iy], zz = u.zt[2][iz];
-  double2 E[3], B[3], J[3];
+  const T k[3] = {(T)u.ks[0][ix], (T)u.ks[1][iy], (T)u.ks[2][iz]};
+  const T zx = (T)u.zt[0][ix], zy = (T)u.zt[1][iy], zz = (T)u.zt[2][iz];
+  C E[3], B[3], J[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     E[a] = u.EB[a * nm + m];
@@ -278,43 +280,43 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs u) {
     J[1] = cscale(J[1], zy);
     J[2] = cscale(J[2], zz);
   }
-  const double2 rn = ld(u.rn + m), rp = ld(u.rp + m);
+  const C rn = u.rn[m], rp = u.rp[m];
   // [k] x F
-  auto cross = [&](const double2* F, double2* o) {
+  auto cross = [&](const C* F, C* o) {
     o[0] = csub(cscale(F[2], k[1]), cscale(F[1], k[2]));
     o[1] = csub(cscale(F[0], k[2]), cscale(F[2], k[0]));
     o[2] = csub(cscale(F[1], k[0]), cscale(F[0], k[1]));
   };
-  double2 kE[3], kB[3], kJ[3];
+  C kE[3], kB[3], kJ[3];
   cross(E, kE);
   cross(B, kB);
   cross(J, kJ);
-  const double2 TC = ld(u.coef + COEF_TC * nm + m), TS = ld(u.coef + COEF_TS * nm + m);
-  const double2 X1 = ld(u.coef + COEF_X1 * nm + m), X2 = ld(u.coef + COEF_X2 * nm + m);
-  const double2 TX3 = ld(u.coef + COEF_TX3 * nm + m), X4 = ld(u.coef + COEF_X4 * nm + m);
+  auto co = [&](int idx) { return cast_c<C>(__ldg(u.coef + idx * nm + m)); };
+  const C TC = co(COEF_TC), TS = co(COEF_TS), X1 = co(COEF_X1), X2 = co(COEF_X2), TX3 = co(COEF_TX3),
+          X4 = co(COEF_X4);
+  const T c2 = (T)u.c2;
   // rho term: i (theta^2 X3 rho^n - X2 rho^{n+1})
-  const double2 rterm = cmuli(csub(cmul(TX3, rn), cmul(X2, rp)));
-  double2 En[3], Bn[3];
+  const C rterm = cmuli(csub(cmul(TX3, rn), cmul(X2, rp)));
+  C En[3], Bn[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     // B^{n+1} = TC B - i TS [k]xE + i X1 [k]xJ
     Bn[a] = cadd(cmul(TC, B[a]), cmuli(csub(cmul(X1, kJ[a]), cmul(TS, kE[a]))));
     // E^{n+1} = TC E + i c^2 TS [k]xB + X4 J + rterm [k]
-    En[a] = cadd(cadd(cmul(TC, E[a]), cmuli(cscale(cmul(TS, kB[a]), u.c2))),
+    En[a] = cadd(cadd(cmul(TC, E[a]), cmuli(cscale(cmul(TS, kB[a]), c2))),
                  cadd(cmul(X4, J[a]), cscale(rterm, k[a])));
   }
-  double2 Ga[3], Gb[3];
+  C Ga[3], Gb[3];
   if (VAR == 2) {
-    const double2 P1 = ld(u.coef + COEF_PSI1 * nm + m), P2 = ld(u.coef + COEF_PSI2 * nm + m);
-    const double2 Y1 = ld(u.coef + COEF_Y1 * nm + m), Y2 = ld(u.coef + COEF_Y2 * nm + m);
-    const double2 Y3 = ld(u.coef + COEF_Y3 * nm + m), Y4 = ld(u.coef + COEF_Y4 * nm + m);
-    const double2 yr = cadd(cmul(Y3, rn), cmul(Y2, rp));
+    const C P1 = co(COEF_PSI1), P2 = co(COEF_PSI2), Y1 = co(COEF_Y1), Y2 = co(COEF_Y2), Y3 = co(COEF_Y3),
+            Y4 = co(COEF_Y4);
+    const C yr = cadd(cmul(Y3, rn), cmul(Y2, rp));
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       // <B> = Psi1 B + i Psi2 [k]xE + i Y1 [k]xJ
       Gb[a] = cadd(cmul(P1, B[a]), cmuli(cadd(cmul(P2, kE[a]), cmul(Y1, kJ[a]))));
       // <E> = Psi1 E - i c^2 Psi2 [k]xB + Y4 J + (Y3 rho^n + Y2 rho^{n+1}) [k]
-      Ga[a] = cadd(csub(cmul(P1, E[a]), cmuli(cscale(cmul(P2, kB[a]), u.c2))),
+      Ga[a] = cadd(csub(cmul(P1, E[a]), cmuli(cscale(cmul(P2, kB[a]), c2))),
                    cadd(cmul(Y4, J[a]), cscale(yr, k[a])));
     }
   } else {
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs u) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) u.J[a * nm + m] = J[a];
   }
-  const double s = u.gscale;
+  const T s = (T)u.gscale;
   if (u.g_mode == 0) {
     u.G[0 * nm + m] = cscale(Ga[0], zx * s);
     u.G[1 * nm + m] = cscale(Ga[1], zy * s);
@@ -342,7 +344,8 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs u) {
     u.G[4 * nm + m] = cscale(Gb[1], zx * zz * s);
     u.G[5 * nm + m] = cscale(Gb[2], zx * zy * s);
   } else {
-    const double2 hx = cconj(u.hs[0][ix]), hy = cconj(u.hs[1][iy]), hz = cconj(u.hs[2][iz]);
+    const C hx = cconj(cast_c<C>(u.hs[0][ix])), hy = cconj(cast_c<C>(u.hs[1][iy])),
+            hz = cconj(cast_c<C>(u.hs[2][iz]));
     u.G[0 * nm + m] = cscale(cmul(Ga[0], hx), s);
     u.G[1 * nm + m] = cscale(cmul(Ga[1], hy), s);
     u.G[2 * nm + m] = cscale(cmul(Ga[2], hz), s);
@@ -365,8 +368,9 @@ __host__ __device__ __forceinline__ int stag_mask(int kind) {
   }
 }
 
+template <class C>
 struct PhaseArgs {
-  CPtr6 in, out;
+  CP6<C> in, out;
   int mask[6];
   int sign;
   double scale;
@@ -374,7 +378,9 @@ struct PhaseArgs {
   int64_t Ny, nzh, nmode;
 };
 
-__global__ void phase_kernel(PhaseArgs p) {
+// phase factors are formed in FP64 and rounded once
+template <class C>
+__global__ void phase_kernel(PhaseArgs<C> p) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= p.nmode) return;
   const int c = blockIdx.y;
@@ -386,18 +392,20 @@ __global__ void phase_kernel(PhaseArgs p) {
   if (mk & 2) f = cmul(f, p.hs[1][iy]);
   if (mk & 4) f = cmul(f, p.hs[2][iz]);
   if (p.sign > 0) f.y = -f.y;
-  p.out.p[c][m] = cmul(p.in.p[c][m], f);
+  p.out.p[c][m] = cmul(p.in.p[c][m], cast_c<C>(f));
 }
 
+template <class C>
 struct NodalArgs {
-  const double2* EB;
-  double2* G;
+  const C* EB;
+  C* G;
   const double* zt[3];
   int64_t Ny, nzh, nmode;
   double scale;
 };
 
-__global__ void to_nodal_kernel(NodalArgs a) {
+template <class C>
+__global__ void to_nodal_kernel(NodalArgs<C> a) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= a.nmode) return;
   const int c = blockIdx.y;
@@ -408,7 +416,7 @@ __global__ void to_nodal_kernel(NodalArgs a) {
   if (mk & 1) z *= a.zt[0][ix];
   if (mk & 2) z *= a.zt[1][iy];
   if (mk & 4) z *= a.zt[2][iz];
-  a.G[c * a.nmode + m] = cscale(a.EB[c * a.nmode + m], z);
+  a.G[c * a.nmode + m] = cscale(a.EB[c * a.nmode + m], (decltype(C().x))z);
 }
 
 // ---------------------------------------------------------------------------
@@ -550,15 +558,16 @@ static const double2* half_shift(const pic_ctx* ctx, int a) {
   return reinterpret_cast<const double2*>(ctx->k1d + 9 * Nmax) + a * Nmax;
 }
 
-pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
-                           int write_j) {
-  UpdArgs u;
-  u.EB = ctx->EBh;
-  u.J = ctx->Jh;
+template <class C>
+pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C* G, int g_mode, int j_yee,
+                          int write_j) {
+  UpdArgs<C> u;
+  u.EB = EB;
+  u.J = J;
   u.rn = rn;
   u.rp = rp;
   u.coef = ctx->coef;
-  u.G = ctx->G;
+  u.G = G;
   for (int a = 0; a < 3; ++a) {
     u.ks[a] = ctx->ks[a];
     u.zt[a] = ctx->zeta[a];
@@ -575,20 +584,31 @@ pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, i
   const int bs = 256;
   const unsigned nb = (unsigned)((ctx->nmode + bs - 1) / bs);
   if (ctx->variant == PIC_PSATD_AVERAGED_GALILEAN)
-    update_kernel<2><<<nb, bs, 0, ctx->stream>>>(u);
+    update_kernel<2, C><<<nb, bs, 0, ctx->stream>>>(u);
   else
-    update_kernel<0><<<nb, bs, 0, ctx->stream>>>(u);
+    update_kernel<0, C><<<nb, bs, 0, ctx->stream>>>(u);
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
+}
+
+pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
+                           int write_j) {
+  return psatd_update_t<double2>(ctx, ctx->EBh, ctx->Jh, rn, rp, ctx->G, g_mode, j_yee, write_j);
+}
+
+pic_status psatd_update32(pic_ctx* ctx, float2* EB, float2* J, const float2* rn, const float2* rp, float2* G,
+                          int g_mode, int j_yee, int write_j) {
+  return psatd_update_t<float2>(ctx, EB, J, rn, rp, G, g_mode, j_yee, write_j);
 }
 
 pic_status psatd_update(pic_ctx* ctx, int cur) {
   return psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], 0, 0, 1);
 }
 
-pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, int ncomp, int sign,
-                       double scale) {
-  PhaseArgs p;
+template <class C>
+pic_status psatd_phase_t(pic_ctx* ctx, CP6<C> in, CP6<C> out, const int* comp_kind, int ncomp, int sign,
+                         double scale) {
+  PhaseArgs<C> p;
   p.in = in;
   p.out = out;
   for (int c = 0; c < ncomp; ++c) p.mask[c] = stag_mask(comp_kind[c]);
@@ -600,15 +620,26 @@ pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, 
   p.nmode = ctx->nmode;
   const int bs = 256;
   dim3 grid((unsigned)((ctx->nmode + bs - 1) / bs), ncomp);
-  phase_kernel<<<grid, bs, 0, ctx->stream>>>(p);
+  phase_kernel<C><<<grid, bs, 0, ctx->stream>>>(p);
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
 
-pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale) {
-  NodalArgs a;
+pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, int ncomp, int sign,
+                       double scale) {
+  return psatd_phase_t<double2>(ctx, in, out, comp_kind, ncomp, sign, scale);
+}
+
+pic_status psatd_phase32(pic_ctx* ctx, CP6<float2> in, CP6<float2> out, const int* comp_kind, int ncomp, int sign,
+                         double scale) {
+  return psatd_phase_t<float2>(ctx, in, out, comp_kind, ncomp, sign, scale);
+}
+
+template <class C>
+pic_status psatd_to_nodal_t(pic_ctx* ctx, const C* EB6, C* G, double scale) {
+  NodalArgs<C> a;
   a.EB = EB6;
-  a.G = ctx->G;
+  a.G = G;
   for (int k = 0; k < 3; ++k) a.zt[k] = ctx->zeta[k];
   a.Ny = ctx->N[1];
   a.nzh = ctx->nzh;
@@ -616,7 +647,15 @@ pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale) {
   a.scale = scale;
   const int bs = 256;
   dim3 grid((unsigned)((ctx->nmode + bs - 1) / bs), 6);
-  to_nodal_kernel<<<grid, bs, 0, ctx->stream>>>(a);
+  to_nodal_kernel<C><<<grid, bs, 0, ctx->stream>>>(a);
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
+}
+
+pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale) {
+  return psatd_to_nodal_t<double2>(ctx, EB6, ctx->G, scale);
+}
+
+pic_status psatd_to_nodal32(pic_ctx* ctx, const float2* EB6, float2* G, double scale) {
+  return psatd_to_nodal_t<float2>(ctx, EB6, G, scale);
 }

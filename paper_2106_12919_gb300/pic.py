@@ -14,6 +14,7 @@ import torch
 from . import build as _build
 
 PIC_OK = 0
+PIC_FP64, PIC_FP32 = 0, 1
 STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_UNSUPPORTED", -3: "PIC_ERR_NOMEM",
           -4: "PIC_ERR_CUDA", -5: "PIC_ERR_CAPACITY", -6: "PIC_ERR_TIMEOUT", -7: "PIC_ERR_NONFINITE"}
 STANDARD, GALILEAN, AVERAGED = 0, 1, 2
@@ -34,6 +35,12 @@ class PicSpecies(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("q", ctypes.c_double), ("m", ctypes.c_double),
                 ("x", _vp), ("y", _vp), ("z", _vp), ("ux", _vp), ("uy", _vp), ("uz", _vp), ("w", _vp),
                 ("id", _vp)]
+
+
+class PicSpecies32(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("q", ctypes.c_double), ("m", ctypes.c_double),
+                ("cell", _vp), ("fx", _vp), ("fy", _vp), ("fz", _vp), ("ux", _vp), ("uy", _vp), ("uz", _vp),
+                ("w", _vp), ("id", _vp)]
 
 
 class PicError(RuntimeError):
@@ -71,6 +78,15 @@ def _load():
         "pic_total_charge": (ctypes.c_int, [_vp, _vp, P(ctypes.c_double)]),
         "pic_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
         "pic_center_to_nodal_static": (ctypes.c_int, [P(ctypes.c_int64), P(ctypes.c_int32), P(_vp), P(_vp), _vp]),
+        "pic_step32": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(_vp), _vp, P(PicSpecies32), ctypes.c_int, ctypes.c_int]),
+        "pic_deposit_rho32": (ctypes.c_int, [_vp, P(PicSpecies32), ctypes.c_int, _vp]),
+        "pic_push_deposit32": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(PicSpecies32), ctypes.c_int, P(_vp), _vp]),
+        "pic_bin32": (ctypes.c_int, [_vp, P(PicSpecies32), _vp]),
+        "pic_fft_forward32": (ctypes.c_int, [_vp, P(_vp), P(_vp), ctypes.c_int]),
+        "pic_fft_inverse32": (ctypes.c_int, [_vp, P(_vp), P(_vp), ctypes.c_int]),
+        "pic_field_energy32": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(ctypes.c_int64), P(ctypes.c_int64),
+                                              P(ctypes.c_double)]),
+        "pic_total_charge32": (ctypes.c_int, [_vp, _vp, P(ctypes.c_double)]),
         "pic_timing_read": (ctypes.c_int, [_vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
@@ -85,7 +101,8 @@ EXPORTS = ("pic_ext_default", "pic_init", "pic_destroy", "pic_last_error", "pic_
            "pic_deposit_rho", "pic_push_deposit", "pic_bin", "pic_num_tiles", "pic_center_to_nodal",
            "pic_center_to_yee", "pic_fft_forward", "pic_fft_inverse", "pic_maxwell_step",
            "pic_coefficient", "pic_field_energy", "pic_total_charge", "pic_timing", "pic_timing_read",
-           "pic_center_to_nodal_static")
+           "pic_center_to_nodal_static", "pic_step32", "pic_deposit_rho32", "pic_push_deposit32", "pic_bin32",
+           "pic_fft_forward32", "pic_fft_inverse32", "pic_field_energy32", "pic_total_charge32")
 
 
 def _ptr(t, n=None):
@@ -93,8 +110,9 @@ def _ptr(t, n=None):
         return None
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch tensor")
-    if not t.is_cuda or t.dtype not in (torch.float64, torch.int64) or not t.is_contiguous():
-        raise ValueError("expected a contiguous CUDA float64/int64 tensor, got %s %s" % (t.device, t.dtype))
+    if not t.is_cuda or t.dtype not in (torch.float64, torch.int64, torch.float32, torch.int32) \
+            or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float/int tensor, got %s %s" % (t.device, t.dtype))
     if n is not None and t.numel() != n:
         raise ValueError("expected %d elements, got %d" % (n, t.numel()))
     return t.data_ptr()
@@ -139,7 +157,65 @@ class Species:
         return PicSpecies(n, self.q, self.m, *p, _ptr(self.id, n) if self.id is not None else None)
 
 
+class Species32:
+    """One FP32-form species: int32 linear cell index, float32 offsets fx, fy, fz in [0, 1),
+    float32 ux, uy, uz, w (+ optional int64 id)."""
+
+    def __init__(self, cell, fx, fy, fz, ux, uy, uz, w, q, m, id=None):
+        self.cell, self.fx, self.fy, self.fz = cell, fx, fy, fz
+        self.ux, self.uy, self.uz, self.w = ux, uy, uz, w
+        self.q, self.m, self.id = float(q), float(m), id
+
+    @property
+    def n(self):
+        return self.cell.numel()
+
+    def arrays(self):
+        return [self.cell, self.fx, self.fy, self.fz, self.ux, self.uy, self.uz, self.w]
+
+    def c_struct(self):
+        n = self.n
+        p = [_ptr(a, n) for a in self.arrays()]
+        return PicSpecies32(n, self.q, self.m, *p, _ptr(self.id, n) if self.id is not None else None)
+
+    @staticmethod
+    def from_positions(x, y, z, ux, uy, uz, w, q, m, shape, dx, device="cuda", id=None):
+        """Host float64 positions -> (cell, offsets) layout on the device (marshalling only)."""
+        import numpy as np
+        idx, off = [], []
+        for a, xa in enumerate((x, y, z)):
+            t = np.asarray(xa, dtype=np.float64) / dx[a]
+            i = np.floor(t)
+            f = (t - i).astype(np.float32)
+            up = f >= np.float32(1.0)            # offset rounded up to 1 in float32
+            f = np.where(up, np.float32(0.0), f)
+            i = (i.astype(np.int64) + up) % shape[a]
+            idx.append(i)
+            off.append(f)
+        cell = ((idx[0] * shape[1] + idx[1]) * shape[2] + idx[2]).astype(np.int32)
+        dev = lambda v, dt: torch.from_numpy(np.ascontiguousarray(v, dtype=dt)).to(device)
+        return Species32(dev(cell, np.int32), dev(off[0], np.float32), dev(off[1], np.float32),
+                         dev(off[2], np.float32), dev(ux, np.float32), dev(uy, np.float32), dev(uz, np.float32),
+                         dev(w, np.float32), q, m, id=id)
+
+    def positions(self, shape, dx):
+        """Device (cell, offsets) -> host float64 positions x, y, z."""
+        import numpy as np
+        c = self.cell.cpu().numpy().astype(np.int64)
+        iz = c % shape[2]
+        iy = (c // shape[2]) % shape[1]
+        ix = c // (shape[1] * shape[2])
+        return [(ix + self.fx.cpu().numpy().astype(np.float64)) * dx[0],
+                (iy + self.fy.cpu().numpy().astype(np.float64)) * dx[1],
+                (iz + self.fz.cpu().numpy().astype(np.float64)) * dx[2]]
+
+
 def _species_array(species):
+    if species and isinstance(species[0], Species32):
+        arr = (PicSpecies32 * max(1, len(species)))()
+        for i, s in enumerate(species):
+            arr[i] = s.c_struct()
+        return arr
     arr = (PicSpecies * max(1, len(species)))()
     for i, s in enumerate(species):
         arr[i] = s.c_struct()
@@ -151,7 +227,7 @@ class Context:
 
     def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
                  v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0,
-                 tile=(8, 8, 8), sort_interval=20, stream=None):
+                 tile=(8, 8, 8), sort_interval=20, stream=None, precision=PIC_FP64):
         self.shape = tuple(int(n) for n in shape)
         self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
         self.nmode = self.shape[0] * self.shape[1] * (self.shape[2] // 2 + 1)
@@ -164,6 +240,8 @@ class Context:
         ext.eps0 = eps0
         ext.tile = _i3(*tile)
         ext.sort_interval = sort_interval
+        ext.precision = precision
+        self.precision = precision
         ext.cuda_stream = self.stream.cuda_stream
         h = _vp()
         st = LIB.pic_init(ctypes.byref(h), _l3(*self.shape), _d3(*dx), dt, shape_order, _i3(*centering_order),
@@ -254,3 +332,40 @@ class Context:
         n = ctypes.c_int64()
         self._check(LIB.pic_timing_read(self.h, stage.encode(), ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    # ---- FP32 form ----
+    def step32(self, E, B, J, rho, species, nsteps):
+        n = self.ncell
+        self._check(LIB.pic_step32(self.h, _parr(E, n), _parr(B, n), _parr(J, n), _ptr(rho, n),
+                                   _species_array(species), len(species), nsteps))
+
+    def deposit_rho32(self, species, rho):
+        self._check(LIB.pic_deposit_rho32(self.h, _species_array(species), len(species), _ptr(rho, self.ncell)))
+
+    def push_deposit32(self, En, Bn, species, Jn, rho):
+        n = self.ncell
+        self._check(LIB.pic_push_deposit32(self.h, _parr(En, n), _parr(Bn, n), _species_array(species),
+                                           len(species), _parr(Jn, n), _ptr(rho, n)))
+
+    def bin32(self, species, offsets=None):
+        self._check(LIB.pic_bin32(self.h, _species_array([species]),
+                                  _ptr(offsets, self.num_tiles() + 1) if offsets is not None else None))
+
+    def fft_forward32(self, real, spec):
+        self._check(LIB.pic_fft_forward32(self.h, _parr(real, self.ncell), _parr(spec, 2 * self.nmode), len(real)))
+
+    def fft_inverse32(self, spec, real):
+        self._check(LIB.pic_fft_inverse32(self.h, _parr(spec, 2 * self.nmode), _parr(real, self.ncell), len(real)))
+
+    def field_energy32(self, E, B, box_lo=None, box_hi=None):
+        out = ctypes.c_double()
+        lo = _l3(*box_lo) if box_lo is not None else None
+        hi = _l3(*box_hi) if box_hi is not None else None
+        self._check(LIB.pic_field_energy32(self.h, _parr(E, self.ncell), _parr(B, self.ncell), lo, hi,
+                                           ctypes.byref(out)))
+        return out.value
+
+    def total_charge32(self, rho):
+        out = ctypes.c_double()
+        self._check(LIB.pic_total_charge32(self.h, _ptr(rho, self.ncell), ctypes.byref(out)))
+        return out.value

@@ -5,8 +5,10 @@
 Default workload: the laser-wakefield box (128 x 128 x 512 cells, dx = dy = 0.2,
 dz = 0.04, dt = dz/c, standard PSATD at infinite order, centering (8, 8, 16),
 cubic shape, 2 electrons per cell = 16,777,216 particles, Gaussian a0 = 2
-laser), plain FP64 form.  One step = one full hybrid cycle (gather, push,
-deposit, centering, FFTs, PSATD update) through pic_step.  Prints one JSON line.
+laser).  One step = one full hybrid cycle (gather, push, deposit, centering,
+FFTs, PSATD update) through pic_step32 (FP32 form, the headline value) and,
+in the same run, pic_step (plain FP64 form, reported beside it with the
+FP32/FP64 ratio).  Prints one JSON line.
 
 --impl libpic (default): K steps of pic_step timed with CUDA events on the
 library's stream after W warm-up steps; value = particle-steps/s over all ranks.
@@ -159,6 +161,8 @@ def main():
     ap.add_argument("--workload", default="laser_wakefield", choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--form", default="both", choices=["both", "fp32", "fp64"],
+                    help="both: FP32 form timed as the headline, FP64 form beside it")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -177,25 +181,84 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2106_12919_gb300 import pic
+
 
     w = make_workload(args.workload)
     p = w["params"]
     shape = p["shape"]
+    ncell = shape[0] * shape[1] * shape[2]
+    forms = ["fp32", "fp64"] if args.form == "both" else [args.form]
+    res = {f: run_form(f, w, args, world, rank, local) for f in forms}
+    head = res[forms[0]]
+    value = head["value"]
+    peaks = measured_peaks()
+    hbm = (peaks or {}).get("hbm_gbs", HBM_PEAK_FALLBACK)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if forms[0] == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(shape), "particles": head["npart"], "form": forms[0],
+                   "shape_order": p["shape_order"], "centering_order": list(p["centering_order"]),
+                   "variant": p["variant"],
+                   "cache": "working set (%.1f GB) > L2 (129 MB); no flush needed" % head["bytes_resident"],
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "cell_updates_per_s": ncell * args.steps * world / (head["ms"] * 1e-3),
+        "stage_ms_per_step": head["stage_ms"],
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+        "e2e": head["e2e"],
+        "roofline": head["roofline"],
+    }
+    if "fp64" in res and forms[0] != "fp64":
+        r64 = res["fp64"]
+        line["fp64_form"] = {"value": r64["value"], "ms_per_step": r64["ms"] / args.steps,
+                             "stage_ms_per_step": r64["stage_ms"], "roofline": r64["roofline"],
+                             "clocks": r64["clocks"], "e2e": r64["e2e"]}
+        line["fp32_over_fp64"] = value / r64["value"]
+    line["roofline"]["peak_note"] = "HBM %.0f GB/s %s; FP64 peak derived: 152 SMs x 4 flop/clk x 2.07 GHz" % (
+        hbm, "of measured" if peaks else "of fallback")
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, _ = run_oracle_sample(args.workload, 4)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_form(form, w, args, world, rank, local):
+    """Time K steps of one form (fp32 | fp64) of the step on the workload; returns a dict of results."""
+    import torch
+    import torch.distributed as dist
+    from paper_2106_12919_gb300 import pic
+
+    p = w["params"]
+    shape = p["shape"]
+    ncell = shape[0] * shape[1] * shape[2]
+    fp32 = form == "fp32"
     stream = torch.cuda.Stream()
     ctx = pic.Context(shape, p["dx"], p["dt"], p["shape_order"], p["centering_order"], p["variant"], p["v_gal"],
-                      p["spectral_order"], p["c"], p["eps0"], stream=stream)
+                      p["spectral_order"], p["c"], p["eps0"], stream=stream,
+                      precision=pic.PIC_FP32 if fp32 else pic.PIC_FP64)
+    fdt = np.float32 if fp32 else np.float64
+    tdt = torch.float32 if fp32 else torch.float64
     with torch.cuda.stream(stream):
-        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=fdt)).cuda()
         E = [dev(a) for a in w["E"]]
         B = [dev(a) for a in w["B"]]
-        J = [torch.zeros(ctx.ncell, dtype=torch.float64, device="cuda") for _ in range(3)]
-        rho = torch.zeros(ctx.ncell, dtype=torch.float64, device="cuda")
-        sp = [pic.Species(dev(s["x"]), dev(s["y"]), dev(s["z"]), dev(s["ux"]), dev(s["uy"]), dev(s["uz"]),
-                          dev(s["w"]), s["q"], s["m"]) for s in w["species"]]
+        J = [torch.zeros(ncell, dtype=tdt, device="cuda") for _ in range(3)]
+        rho = torch.zeros(ncell, dtype=tdt, device="cuda")
+        if fp32:
+            sp = [pic.Species32.from_positions(s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["q"],
+                                               s["m"], shape, p["dx"]) for s in w["species"]]
+        else:
+            sp = [pic.Species(dev(s["x"]), dev(s["y"]), dev(s["z"]), dev(s["ux"]), dev(s["uy"]), dev(s["uz"]),
+                              dev(s["w"]), s["q"], s["m"]) for s in w["species"]]
+    torch.cuda.synchronize()
     npart = sum(s.n for s in sp)
-    ctx.deposit_rho(sp, rho)
-    ctx.step(E, B, J, rho, sp, args.warmup)
+    step = ctx.step32 if fp32 else ctx.step
+    (ctx.deposit_rho32 if fp32 else ctx.deposit_rho)(sp, rho)
+    step(E, B, J, rho, sp, args.warmup)
     ctx.sync()
 
     # ---- timed region: K steps of pic_step, inputs resident in HBM ----
@@ -208,7 +271,7 @@ def main():
     ctx.timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ctx.step(E, B, J, rho, sp, args.steps)
+    step(E, B, J, rho, sp, args.steps)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
@@ -226,23 +289,21 @@ def main():
 
     # ---- end to end: host (pinned) state -> device, one pic_step, field energy back ----
     ke = args.e2e_steps or max(3, min(args.steps, 10))
-    host = [t.cpu().pin_memory() for t in E + B + [rho]] + \
-           [a.cpu().pin_memory() for s in sp for a in s.arrays()]
     devs = E + B + [rho] + [a for s in sp for a in s.arrays()]
+    host = [t.cpu().pin_memory() for t in devs]
     h2d = sum(h.numel() * h.element_size() for h in host)
+    energy = ctx.field_energy32 if fp32 else ctx.field_energy
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    t0 = e0.__class__(enable_timing=True)
-    t1 = e0.__class__(enable_timing=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    energies = []
     for _ in range(ke):
         with torch.cuda.stream(stream):
             for d, h in zip(devs, host):
                 d.copy_(h, non_blocking=True)
-        ctx.step(E, B, J, rho, sp, 1)
-        energies.append(ctx.field_energy(E, B))
+        step(E, B, J, rho, sp, 1)
+        energy(E, B)
     t1.record(stream)
     t1.synchronize()
     e2e_ms = t0.elapsed_time(t1)
@@ -250,49 +311,40 @@ def main():
         t = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e_value = npart * ke * world / (e2e_ms * 1e-3)
+    e2e = {"value": npart * ke * world / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": 8, "steps": ke,
+           "note": "per step: pinned H2D of E, B, rho and all particles, pic_step(1), field energy read back"}
 
-    # ---- roofline of the dominant kernel (FP64 form: gather/push/deposit, FP64-ALU bound) ----
+    # ---- roofline of the dominant kernel (gather + push + deposit) ----
     push_ms, push_n = stage["push"]
     push_avg_s = push_ms * 1e-3 / max(push_n, 1)
-    per_launch_particles = npart / max(1, len(sp))
-    flops = push_flops_per_particle(p["shape_order"]) * per_launch_particles
-    achieved = flops / push_avg_s / 1e12
+    per_launch = npart / max(1, len(sp))
     peaks = measured_peaks()
     hbm = (peaks or {}).get("hbm_gbs", HBM_PEAK_FALLBACK)
-    roofline = {"kernel": "push_kernel (gather + Boris + deposit)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None,
-                "peak_note": "FP64 peak derived: 152 SMs x 4 flop/clk x 2.07 GHz; HBM %.0f GB/s (%s)" % (
-                    hbm, "of measured" if peaks else "of fallback"),
-                "algorithmic_bytes_per_particle": 104,
-                "hbm_frac": 104 * per_launch_particles / push_avg_s / 1e9 / hbm}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": list(shape), "particles": npart, "form": "fp64",
-                   "shape_order": p["shape_order"], "centering_order": list(p["centering_order"]),
-                   "variant": p["variant"], "cache": "working set (~4.5 GB) > L2 (129 MB); no flush needed",
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "cell_updates_per_s": shape[0] * shape[1] * shape[2] * args.steps * world / (ms * 1e-3),
-        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stage.items() if k != "all"},
-        "gpu_launches": stage["all"][1],
-        "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
-                "steps": ke, "note": "per step: pinned H2D of E, B, rho and all particles, pic_step(1), "
-                                    "field energy read back"},
-        "roofline": roofline,
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, _ = run_oracle_sample(args.workload, 4)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    if fp32:
+        # 32 B read + 28 B written per particle; nodal E, B read (24 B) and J, rho deposited (16 B) per cell
+        nbytes = 60 * per_launch + 40 * ncell
+        achieved = nbytes / push_avg_s / 1e9
+        roofline = {"kernel": "push32_kernel (gather + Boris + deposit)", "bound": "hbm", "achieved": achieved,
+                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "algorithmic_bytes": "60 B/particle + 40 B/cell per launch"}
+    else:
+        flops = push_flops_per_particle(p["shape_order"]) * per_launch
+        achieved = flops / push_avg_s / 1e12
+        roofline = {"kernel": "push_kernel (gather + Boris + deposit)", "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": None, "algorithmic_flops": "22 (p+1)^3 + 250 per particle",
+                    "hbm_frac": 104 * per_launch / push_avg_s / 1e9 / hbm}
+    esz = 4 if fp32 else 8
+    resident = (10 * ncell * esz + sum(sum(a.numel() * a.element_size() for a in s.arrays()) for s in sp)
+                + 40 * ncell * esz) / 1e9
+    out = {"value": value, "ms": ms, "npart": npart, "clocks": clocks, "e2e": e2e, "roofline": roofline,
+           "stage_ms": {k: v[0] / args.steps for k, v in stage.items() if k != "all"},
+           "launches": stage["all"][1], "bytes_resident": resident}
     ctx.close()
+    del E, B, J, rho, sp, host, devs
+    torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

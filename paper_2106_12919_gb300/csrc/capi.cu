@@ -132,9 +132,11 @@ void pic_destroy(pic_ctx* ctx) {
   if (!ctx) return;
   void* ptrs[] = {ctx->k1d, ctx->twid[0], ctx->twid[1], ctx->twid[2], ctx->coef, ctx->EBh,
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
-                  ctx->bin_cursor, ctx->bin_tmp};
+                  ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q)
+    if (ctx->sp_off[q]) cudaFree(ctx->sp_off[q]);
   timers_free(ctx);
   delete ctx;
 }
@@ -198,6 +200,7 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   ctx->eps0 = e.eps0;
   ctx->sort_interval = e.sort_interval;
   ctx->precision = e.precision;
+  for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) ctx->sp_off_n[q] = -1;
   ctx->stream = reinterpret_cast<cudaStream_t>(e.cuda_stream);
   ctx->ncell = grid[0] * grid[1] * grid[2];
   ctx->nzh = grid[2] / 2 + 1;

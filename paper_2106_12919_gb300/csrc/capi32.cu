@@ -211,18 +211,32 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   const float* Bn[3] = {nd + 3 * nc, nd + 4 * nc, nd + 5 * nc};
   float* jn = Jn(ctx);
   float* Jnp[3] = {jn, jn + nc, jn + 2 * nc};
+  const bool tiled = ctx->sort_interval > 0 && tiled_push_fits(ctx);
   for (int s = 0; s < nsteps; ++s) {
     const bool last = s == nsteps - 1;
-    if (ctx->sort_interval > 0 && ctx->steps_done % ctx->sort_interval == 0)
+    // bin at the first step of every call (the caller may have changed the particles) and then
+    // every sort_interval steps; the tiled push uses the ranges of the species' last binning
+    if (ctx->sort_interval > 0 && (s == 0 || ctx->steps_done % ctx->sort_interval == 0))
       for (int q = 0; q < n_species; ++q) {
         StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 3 : 1);
-        PIC_TRY32(particles_bin32(ctx, &sp[q], nullptr));
+        int64_t* off = nullptr;
+        if (tiled && q < PIC_MAX_BINNED_SPECIES) {
+          if (!ctx->sp_off[q]) {
+            PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
+          }
+          off = ctx->sp_off[q];
+          ctx->sp_off_n[q] = sp[q].n;
+        }
+        PIC_TRY32(particles_bin32(ctx, &sp[q], off));
       }
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(jn, 0, 3 * nc * sizeof(float), ctx->stream));
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(rho, 0, nc * sizeof(float), ctx->stream));
     for (int q = 0; q < n_species; ++q) {
       StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
-      PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
+      if (tiled && q < PIC_MAX_BINNED_SPECIES && ctx->sp_off[q] && ctx->sp_off_n[q] == sp[q].n)
+        PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q]));
+      else
+        PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
     }
     CRP6<float> in;
     CP6<float2> out;

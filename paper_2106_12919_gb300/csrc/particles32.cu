@@ -102,6 +102,58 @@ __device__ __forceinline__ void deposit_node_block(const Push32Args& a, int ix, 
   }
 }
 
+// Shared-memory deposit window of one tile: nodes [org, org + W) per axis
+// (unwrapped coordinates), four FP32 components (J^x, J^y, J^z, rho).
+struct Window {
+  float* acc;     // [4][W0][W1][W2]
+  int org[3];
+  int W[3];
+};
+
+// Deposit one particle's (P+1)^3 block: inside the window with shared-memory
+// atomics, outside it (a particle that left its tile since the last binning)
+// with global atomics.  comp0 = 0 deposits (v0, v1, v2) into J, comp0 = 3 deposits r into rho.
+template <int P>
+__device__ __forceinline__ void deposit_window(const Push32Args& a, const Window& win, int ix, int iy, int iz,
+                                               float fx, float fy, float fz, float v0, float v1, float v2, float r,
+                                               bool j) {
+  constexpr int NS = P + 1;
+  int lx, ly, lz;
+  float Sx[NS], Sy[NS], Sz[NS];
+  shape32<P>(ix, fx, lx, Sx);
+  shape32<P>(iy, fy, ly, Sy);
+  shape32<P>(iz, fz, lz, Sz);
+  const int wx = lx - win.org[0], wy = ly - win.org[1], wz = lz - win.org[2];
+  const bool inside = wx >= 0 && wy >= 0 && wz >= 0 && wx + NS <= win.W[0] && wy + NS <= win.W[1] &&
+                      wz + NS <= win.W[2];
+  if (!inside) {
+    if (j) deposit_node_block<P>(a, ix, iy, iz, fx, fy, fz, v0, v1, v2, 0.f, true);
+    else deposit_node_block<P>(a, ix, iy, iz, fx, fy, fz, 0.f, 0.f, 0.f, r, false);
+    return;
+  }
+  const int plane = win.W[1] * win.W[2];
+  const int vol = win.W[0] * plane;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+#pragma unroll
+    for (int jj = 0; jj < NS; ++jj) {
+      const float sxy = Sx[i] * Sy[jj];
+      float* row = win.acc + (wx + i) * plane + (wy + jj) * win.W[2] + wz;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const float s = sxy * Sz[k];
+        if (j) {
+          atomicAdd(row + k, s * v0);
+          atomicAdd(row + vol + k, s * v1);
+          atomicAdd(row + 2 * vol + k, s * v2);
+        } else {
+          atomicAdd(row + 3 * vol + k, s * r);
+        }
+      }
+    }
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -171,6 +223,146 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
   deposit_node_block<P>(a, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
 }
 
+// Tiled form: one CTA per particle tile (ranges from the last binning).  Gathers
+// through L1, accumulates J and rho in a shared-memory window covering the tile
+// plus two guard cells on each side (enough for a cubic shape and a move of
+// up to one cell), then flushes the window once with global atomics.
+struct TileArgs {
+  const int64_t* off;  // [n_tiles + 1] particle ranges
+  int T[3];            // tile edge (cells)
+  int nt[3];           // tiles per axis
+  int W[3];            // window edge = T + 5
+};
+
+// The tile's nodal E, B (nodes [T0 - 1, T0 + T + 2) per axis) are staged once in
+// shared memory as 6-float records, so the gather of a fresh particle is three
+// 8-byte shared loads per node; a particle whose gather block is outside the
+// staged nodes (it left the tile since the last binning) gathers from global memory.
+template <int P>
+__global__ void __launch_bounds__(256, 3) push32_tile_kernel(Push32Args a, TileArgs t) {
+  extern __shared__ float smem[];
+  const int tile = blockIdx.x;
+  const int tz = tile % t.nt[2], ty = (tile / t.nt[2]) % t.nt[1], tx = tile / (t.nt[1] * t.nt[2]);
+  Window win;
+  win.org[0] = tx * t.T[0] - 2;
+  win.org[1] = ty * t.T[1] - 2;
+  win.org[2] = tz * t.T[2] - 2;
+  for (int d = 0; d < 3; ++d) win.W[d] = t.W[d];
+  const int vol = t.W[0] * t.W[1] * t.W[2];
+  win.acc = smem;
+  // gather window: nodes [T0 - 1, T0 + T + 2), i.e. G = T + 3 per axis, record of 6 floats (+ pad to 6)
+  const int G0 = t.T[0] + 3, G1 = t.T[1] + 3, G2 = t.T[2] + 3;
+  const int gvol = G0 * G1 * G2;
+  float2* fld = reinterpret_cast<float2*>(smem + 4 * vol);  // [gvol][3] float2
+  const int go0 = tx * t.T[0] - 1, go1 = ty * t.T[1] - 1, go2 = tz * t.T[2] - 1;
+  for (int e = threadIdx.x; e < 4 * vol; e += blockDim.x) smem[e] = 0.0f;
+  for (int e = threadIdx.x; e < gvol; e += blockDim.x) {
+    const int k = e % G2, r = e / G2;
+    const int j = r % G1, i = r / G1;
+    const int o = (((go0 + i) & a.mask[0]) * (int)a.Ny + ((go1 + j) & a.mask[1])) * (int)a.Nz + ((go2 + k) & a.mask[2]);
+    fld[3 * e + 0] = make_float2(__ldg(a.F[0] + o), __ldg(a.F[1] + o));
+    fld[3 * e + 1] = make_float2(__ldg(a.F[2] + o), __ldg(a.F[3] + o));
+    fld[3 * e + 2] = make_float2(__ldg(a.F[4] + o), __ldg(a.F[5] + o));
+  }
+  __syncthreads();
+  constexpr int NS = P + 1;
+  const int p0 = (int)t.off[tile], p1 = (int)t.off[tile + 1];
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const int c = a.cell[p];
+    const int ix = (c >> (a.shz + a.shy)) & a.mask[0], iy = (c >> a.shz) & a.mask[1], iz = c & a.mask[2];
+    const float fx = a.fx[p], fy = a.fy[p], fz = a.fz[p];
+    const float qw = a.w[p] * a.qw_scale;
+    int lx, ly, lz;
+    float Sx[NS], Sy[NS], Sz[NS];
+    shape32<P>(ix, fx, lx, Sx);
+    shape32<P>(iy, fy, ly, Sy);
+    shape32<P>(iz, fz, lz, Sz);
+    float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int gx = lx - go0, gy = ly - go1, gz = lz - go2;
+    if (gx >= 0 && gy >= 0 && gz >= 0 && gx + NS <= G0 && gy + NS <= G1 && gz + NS <= G2) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          const float sxy = Sx[i] * Sy[j];
+          const float2* row = fld + 3 * (((gx + i) * G1 + (gy + j)) * G2 + gz);
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            const float s = sxy * Sz[k];
+            const float2 v0 = row[3 * k], v1 = row[3 * k + 1], v2 = row[3 * k + 2];
+            f[0] += s * v0.x;
+            f[1] += s * v0.y;
+            f[2] += s * v1.x;
+            f[3] += s * v1.y;
+            f[4] += s * v2.x;
+            f[5] += s * v2.y;
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        const int ox = ((lx + i) & a.mask[0]) * (int)a.Ny;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          const int oy = (ox + ((ly + j) & a.mask[1])) * (int)a.Nz;
+          const float sxy = Sx[i] * Sy[j];
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            const int o = oy + ((lz + k) & a.mask[2]);
+            const float s = sxy * Sz[k];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) f[q] += s * __ldg(a.F[q] + o);
+          }
+        }
+      }
+    }
+    const float kq = a.qm_half_dt;
+    const float umx = a.ux[p] + kq * f[0], umy = a.uy[p] + kq * f[1], umz = a.uz[p] + kq * f[2];
+    const float igm = rsqrtf(1.0f + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
+    const float tx_ = kq * f[3] * igm, ty_ = kq * f[4] * igm, tz_ = kq * f[5] * igm;
+    const float s2 = 2.0f / (1.0f + tx_ * tx_ + ty_ * ty_ + tz_ * tz_);
+    const float sx = s2 * tx_, sy = s2 * ty_, sz = s2 * tz_;
+    const float upx = umx + (umy * tz_ - umz * ty_);
+    const float upy = umy + (umz * tx_ - umx * tz_);
+    const float upz = umz + (umx * ty_ - umy * tx_);
+    const float ux = umx + (upy * sz - upz * sy) + kq * f[0];
+    const float uy = umy + (upz * sx - upx * sz) + kq * f[1];
+    const float uz = umz + (upx * sy - upy * sx) + kq * f[2];
+    const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
+    const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
+    const float dX = a.dtdx[0] * (vx - a.vg[0]), dY = a.dtdx[1] * (vy - a.vg[1]), dZ = a.dtdx[2] * (vz - a.vg[2]);
+    float mfx, mfy, mfz, nfx, nfy, nfz;
+    const int mx = ix + move_offset(fx, 0.5f * dX, mfx), my = iy + move_offset(fy, 0.5f * dY, mfy),
+              mz = iz + move_offset(fz, 0.5f * dZ, mfz);
+    const int nx = ix + move_offset(fx, dX, nfx), ny = iy + move_offset(fy, dY, nfy),
+              nz = iz + move_offset(fz, dZ, nfz);
+    a.cell[p] = (((nx & a.mask[0]) * (int)a.Ny + (ny & a.mask[1])) * (int)a.Nz) + (nz & a.mask[2]);
+    a.fx[p] = nfx;
+    a.fy[p] = nfy;
+    a.fz[p] = nfz;
+    a.ux[p] = ux;
+    a.uy[p] = uy;
+    a.uz[p] = uz;
+    deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
+    deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
+  }
+  __syncthreads();
+  // flush the window: node (i, j, k) of the window is global node org + (i, j, k), wrapped
+  float* dst[4] = {a.J[0], a.J[1], a.J[2], a.rho};
+  for (int e = threadIdx.x; e < vol; e += blockDim.x) {
+    const int k = e % t.W[2], r = e / t.W[2];
+    const int j = r % t.W[1], i = r / t.W[1];
+    const int o = (((win.org[0] + i) & a.mask[0]) * (int)a.Ny + ((win.org[1] + j) & a.mask[1])) * (int)a.Nz +
+                  ((win.org[2] + k) & a.mask[2]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float v = smem[q * vol + e];
+      if (v != 0.0f) atomicAdd(dst[q] + o, v);
+    }
+  }
+}
+
 int ilog2(int64_t v) {
   int r = 0;
   while ((int64_t(1) << r) < v) ++r;
@@ -216,82 +408,163 @@ pic_status launch_push32(pic_ctx* ctx, const Push32Args& a) {
   return PIC_OK;
 }
 
+pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t* off) {
+  if (a.n == 0) return PIC_OK;
+  TileArgs t;
+  t.off = off;
+  int vol = 1;
+  for (int d = 0; d < 3; ++d) {
+    t.T[d] = ctx->tile[d];
+    t.nt[d] = (int)(ctx->N[d] / ctx->tile[d]);
+    t.W[d] = ctx->tile[d] + 5;
+    vol *= t.W[d];
+  }
+  size_t gvol = 1;
+  for (int d = 0; d < 3; ++d) gvol *= (size_t)(ctx->tile[d] + 3);
+  const size_t smem = 4 * (size_t)vol * sizeof(float) + 6 * gvol * sizeof(float);
+  const unsigned nb = (unsigned)ctx->n_tiles;
+  if (smem > 48 * 1024) {
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  switch (ctx->shape_order) {
+    case 1: push32_tile_kernel<1><<<nb, 256, smem, ctx->stream>>>(a, t); break;
+    case 2: push32_tile_kernel<2><<<nb, 256, smem, ctx->stream>>>(a, t); break;
+    default: push32_tile_kernel<3><<<nb, 256, smem, ctx->stream>>>(a, t); break;
+  }
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
+
 // ---------------------------------------------------------------------------
-// tile binning of the FP32 SoA (integer only: tile from the cell index)
+// binning of the FP32 SoA: counting sort by cell in tile-major order
+// key = tile * cells_per_tile + local cell (z fastest), so particles end up grouped by
+// tile and, inside a tile, ordered by cell (integer only: from the cell index)
 // ---------------------------------------------------------------------------
-struct Bin32Args {
+struct Key32Args {
   const int32_t* cell;
   int64_t n;
   int shz, shy;
   int mask[3];
   int tshift[3];
+  int tmask[3];
   int64_t nty, ntz;
-  int32_t* tid;
-  unsigned long long* counts;
+  int lshift_y, lshift_z;  // log2 of the tile edge in y, z (local cell index)
+  int cpt_shift;           // log2 cells per tile
+  int32_t* key;
+  uint32_t* counts;
 };
 
-__global__ void tile_id32_kernel(Bin32Args a) {
+__global__ void key32_kernel(Key32Args a) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= a.n) return;
   const int c = a.cell[p];
   const int cx = (c >> (a.shz + a.shy)) & a.mask[0], cy = (c >> a.shz) & a.mask[1], cz = c & a.mask[2];
   const int t = (int)(((cx >> a.tshift[0]) * a.nty + (cy >> a.tshift[1])) * a.ntz + (cz >> a.tshift[2]));
-  a.tid[p] = t;
+  const int local = ((((cx & a.tmask[0]) << a.lshift_y) | (cy & a.tmask[1])) << a.lshift_z) | (cz & a.tmask[2]);
+  const int k = (t << a.cpt_shift) | local;
+  a.key[p] = k;
   const unsigned active = __activemask();
-  const unsigned peers = __match_any_sync(active, t);
+  const unsigned peers = __match_any_sync(active, k);
   const int leader = __ffs(peers) - 1;
-  if ((int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + t, (unsigned long long)__popc(peers));
+  if ((int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + k, (uint32_t)__popc(peers));
 }
 
-__global__ void __launch_bounds__(1024) scan32_kernel(const unsigned long long* cnt, int64_t* off, int64_t n) {
-  __shared__ unsigned long long part[1024];
-  const int T = blockDim.x;
-  const int64_t chunk = (n + T - 1) / T;
-  const int64_t b = threadIdx.x * chunk, e = min(n, b + chunk);
-  unsigned long long s = 0;
-  for (int64_t i = b; i < e; ++i) s += cnt[i];
+// exclusive scan, phase 1: each block scans 4096 counts in place (to offsets within the block)
+// and writes its total to bsum[block]
+constexpr int kScanBlock = 4096;
+__global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n, uint32_t* bsum) {
+  __shared__ uint32_t part[1024];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  uint32_t x[4];
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = base + threadIdx.x * 4 + q;
+    x[q] = i < n ? v[i] : 0u;
+    s += x[q];
+  }
   part[threadIdx.x] = s;
   __syncthreads();
-  for (int d = 1; d < T; d <<= 1) {
-    unsigned long long v = threadIdx.x >= d ? part[threadIdx.x - d] : 0ull;
+  for (int d = 1; d < 1024; d <<= 1) {
+    const uint32_t t = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
     __syncthreads();
-    part[threadIdx.x] += v;
+    part[threadIdx.x] += t;
     __syncthreads();
   }
-  unsigned long long run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0ull;
+  uint32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0u;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = base + threadIdx.x * 4 + q;
+    if (i < n) v[i] = run;
+    run += x[q];
+  }
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = part[1023];
+}
+
+// phase 2: one CTA scans the block totals (exclusive) and writes the grand total
+__global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* bsum, int64_t nb, uint32_t* total) {
+  __shared__ uint32_t part[1024];
+  const int64_t chunk = (nb + 1023) / 1024;
+  const int64_t b = threadIdx.x * chunk, e = min(nb, b + chunk);
+  uint32_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += bsum[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    const uint32_t t = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += t;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0u;
   for (int64_t i = b; i < e; ++i) {
-    off[i] = (int64_t)run;
-    run += cnt[i];
+    const uint32_t c = bsum[i];
+    bsum[i] = run;
+    run += c;
   }
-  if (threadIdx.x == T - 1) off[n] = (int64_t)part[T - 1];
+  if (threadIdx.x == 1023) *total = part[1023];
+}
+
+// phase 3: add the block offsets; also emit the per-tile ranges off[t] = cell offset of the tile's first key
+__global__ void scan_add_kernel(uint32_t* v, int64_t n, const uint32_t* bsum, int cpt_shift, int64_t* tile_off,
+                                int64_t n_tiles, const uint32_t* total) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t o = v[i] + bsum[i / kScanBlock];
+    v[i] = o;
+    if ((i & ((int64_t(1) << cpt_shift) - 1)) == 0) tile_off[i >> cpt_shift] = (int64_t)o;
+  }
+  if (i == 0) tile_off[n_tiles] = (int64_t)*total;
 }
 
 struct Scatter32Args {
-  const uint32_t* src[9];  // cell, fx, fy, fz, ux, uy, uz, w as 32-bit words
-  uint32_t* dst[9];
+  const uint32_t* src[8];  // cell, fx, fy, fz, ux, uy, uz, w as 32-bit words
+  uint32_t* dst[8];
   const unsigned long long* id_src;
   unsigned long long* id_dst;
-  int nfield;
   int64_t n;
-  const int32_t* tid;
-  const int64_t* off;
-  unsigned long long* cursor;
+  const int32_t* key;
+  const uint32_t* off;     // exclusive offsets per key
+  uint32_t* cursor;        // zeroed
 };
 
 __global__ void scatter32_kernel(Scatter32Args a) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= a.n) return;
-  const int t = a.tid[p];
+  const int k = a.key[p];
   const unsigned active = __activemask();
-  const unsigned peers = __match_any_sync(active, t);
+  const unsigned peers = __match_any_sync(active, k);
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
   const int rank = __popc(peers & ((1u << lane) - 1u));
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(a.cursor + t, (unsigned long long)__popc(peers));
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(a.cursor + k, (uint32_t)__popc(peers));
   base = __shfl_sync(peers, base, leader);
-  const int64_t q = a.off[t] + (int64_t)base + rank;
-  for (int f = 0; f < a.nfield; ++f) a.dst[f][q] = a.src[f][p];
+  const int64_t q = (int64_t)a.off[k] + base + rank;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) a.dst[f][q] = a.src[f][p];
   if (a.id_src) a.id_dst[q] = a.id_src[p];
 }
 
@@ -310,6 +583,28 @@ pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float*
   return launch_push32(ctx, a);
 }
 
+bool tiled_push_fits(const pic_ctx* ctx) {
+  size_t vol = 1, gvol = 1;
+  for (int d = 0; d < 3; ++d) {
+    vol *= (size_t)(ctx->tile[d] + 5);
+    gvol *= (size_t)(ctx->tile[d] + 3);
+  }
+  return (4 * vol + 6 * gvol) * sizeof(float) <= 160 * 1024 && ctx->ncell < (int64_t(1) << 31);
+}
+
+pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
+                                  const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets) {
+  Push32Args a = make_args32(ctx, sp);
+  for (int c = 0; c < 3; ++c) {
+    a.F[c] = En[c];
+    a.F[3 + c] = Bn[c];
+    a.J[c] = J[c];
+  }
+  a.rho = rho;
+  a.gather = 1;
+  return launch_push32_tiled(ctx, a, offsets);
+}
+
 pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float* rho) {
   Push32Args a = make_args32(ctx, sp);
   for (int c = 0; c < 6; ++c) a.F[c] = nullptr;
@@ -321,12 +616,19 @@ pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float*
 
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out) {
   const int64_t n = sp->n;
-  // scratch: tile ids (int32) and 8 x n 32-bit words + n ids, inside the FP64 binning buffers
   pic_status st = particles_bin_capacity(ctx, n > 0 ? n : 1);
   if (st != PIC_OK) return st;
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ctx->bin_cursor);
-  PIC_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, ctx->n_tiles * sizeof(int64_t), ctx->stream));
-  Bin32Args b;
+  const int64_t ncell = ctx->ncell;
+  const int64_t nblk = (ncell + kScanBlock - 1) / kScanBlock;
+  if (!ctx->cell_counts) {
+    // counts/offsets per cell, block sums, total
+    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->cell_counts, (ncell + nblk + 2) * sizeof(uint32_t)));
+  }
+  uint32_t* counts = ctx->cell_counts;
+  uint32_t* bsum = counts + ncell;
+  uint32_t* total = bsum + nblk;
+  PIC_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, ncell * sizeof(uint32_t), ctx->stream));
+  Key32Args b;
   b.cell = sp->cell;
   b.n = n;
   b.shz = ilog2(ctx->N[2]);
@@ -334,27 +636,34 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   for (int d = 0; d < 3; ++d) {
     b.mask[d] = (int)ctx->N[d] - 1;
     b.tshift[d] = ilog2(ctx->tile[d]);
+    b.tmask[d] = ctx->tile[d] - 1;
   }
   b.nty = ctx->N[1] / ctx->tile[1];
   b.ntz = ctx->N[2] / ctx->tile[2];
-  b.tid = ctx->bin_tid;
-  b.counts = cnt;
+  b.lshift_y = ilog2(ctx->tile[1]);
+  b.lshift_z = ilog2(ctx->tile[2]);
+  b.cpt_shift = ilog2(ctx->tile[0]) + ilog2(ctx->tile[1]) + ilog2(ctx->tile[2]);
+  b.key = ctx->bin_tid;
+  b.counts = counts;
   const int bs = 256;
   const unsigned nb = (unsigned)((n + bs - 1) / bs);
   if (n > 0) {
-    tile_id32_kernel<<<nb, bs, 0, ctx->stream>>>(b);
+    key32_kernel<<<nb, bs, 0, ctx->stream>>>(b);
     PIC_LAUNCH_CHECK(ctx);
   }
-  scan32_kernel<<<1, 1024, 0, ctx->stream>>>(cnt, ctx->bin_counts, ctx->n_tiles);
+  scan_block_kernel<<<(unsigned)nblk, 1024, 0, ctx->stream>>>(counts, ncell, bsum);
   PIC_LAUNCH_CHECK(ctx);
-  if (offsets_out)
-    PIC_CUDA_TRY(ctx, cudaMemcpyAsync(offsets_out, ctx->bin_counts, (ctx->n_tiles + 1) * sizeof(int64_t),
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
+  scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(bsum, nblk, total);
+  PIC_LAUNCH_CHECK(ctx);
+  int64_t* tile_off = offsets_out ? offsets_out : ctx->bin_counts;
+  scan_add_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, ctx->stream>>>(counts, ncell, bsum, b.cpt_shift,
+                                                                           tile_off, ctx->n_tiles, total);
+  PIC_LAUNCH_CHECK(ctx);
   if (n == 0) return PIC_OK;
-  PIC_CUDA_TRY(ctx, cudaMemsetAsync(cnt, 0, ctx->n_tiles * sizeof(int64_t), ctx->stream));
+  if (!ctx->cell_cursor) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->cell_cursor, ncell * sizeof(uint32_t)));
+  PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_cursor, 0, ncell * sizeof(uint32_t), ctx->stream));
   Scatter32Args s;
   void* fields[8] = {sp->cell, sp->fx, sp->fy, sp->fz, sp->ux, sp->uy, sp->uz, sp->w};
-  s.nfield = 8;
   uint32_t* tmp = reinterpret_cast<uint32_t*>(ctx->bin_tmp);
   for (int f = 0; f < 8; ++f) {
     s.src[f] = static_cast<const uint32_t*>(fields[f]);
@@ -363,9 +672,9 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   s.id_src = reinterpret_cast<const unsigned long long*>(sp->id);
   s.id_dst = reinterpret_cast<unsigned long long*>(ctx->bin_tmp + 4 * ctx->bin_cap);  // words 8n..10n
   s.n = n;
-  s.tid = ctx->bin_tid;
-  s.off = ctx->bin_counts;
-  s.cursor = cnt;
+  s.key = ctx->bin_tid;
+  s.off = counts;
+  s.cursor = ctx->cell_cursor;
   scatter32_kernel<<<nb, bs, 0, ctx->stream>>>(s);
   PIC_LAUNCH_CHECK(ctx);
   for (int f = 0; f < 8; ++f)

@@ -10,6 +10,7 @@
 #include "pic.h"
 
 #define PIC_MAX_CENTER_M 16  // centering order 2m <= 32
+#define PIC_MAX_BINNED_SPECIES 8  // species that keep per-tile ranges between steps (FP32 form)
 
 // ---------------------------------------------------------------------------
 // complex helpers (double2 / float2 as (re, im))
@@ -116,8 +117,13 @@ struct pic_ctx {
   void* scan_tmp;
   size_t scan_tmp_bytes;
   int64_t n_tiles;
+  uint32_t* cell_counts;  // FP32 binning: per-cell counts -> offsets, block sums, total
+  uint32_t* cell_cursor;  // FP32 binning: per-cell scatter cursors
 
   int64_t steps_done;
+  // FP32 form: per-species tile ranges of the last binning inside pic_step32
+  int64_t* sp_off[PIC_MAX_BINNED_SPECIES];
+  int64_t sp_off_n[PIC_MAX_BINNED_SPECIES];   // particle count they were built for, -1 = invalid
   Timers timers;
   char err[256];
 };
@@ -198,6 +204,11 @@ pic_status particles_bin_capacity(pic_ctx* ctx, int64_t n);
 pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                             const pic_species32* sp, float* const J[3], float* rho);
 pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float* rho);
+// Tiled push: one CTA per tile over the ranges offsets[n_tiles + 1] of the last binning,
+// shared-memory deposit window per tile.  Correct for any order (out-of-window deposits go global).
+bool tiled_push_fits(const pic_ctx* ctx);  // deposit window of the tile fits in shared memory
+pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
+                                  const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets);
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out);
 
 // center.cu -------------------------------------------------------------------

@@ -167,6 +167,43 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
                     double* rho, const pic_species* sp, int n_species, int nsteps);
 
 /*
+ * Per-particle adjoint arrays of one species (reverse mode): adjoints of the
+ * positions x, y, z and momenta ux, uy, uz, device FP64 arrays of n elements,
+ * index-aligned with the species they belong to.
+ */
+typedef struct {
+  int64_t n;
+  double* x;
+  double* y;
+  double* z;
+  double* ux;
+  double* uy;
+  double* uz;
+} pic_species_adjoint;
+
+/*
+ * pic_adjoint_step: reverse mode of one pic_step (FP64 form; standard and
+ * Galilean variants).  The paper states the forward method only; the reverse
+ * applies the transpose of each map of the hybrid cycle in reverse order:
+ * the PSATD update of Sec. 4 (per mode, the conjugate transpose of its
+ * coefficient matrix), the centering of Sec. 3 (transposes), the direct
+ * deposits and the gather (transposes of each other, plus the B-spline
+ * derivative for the positions), x^{n+1} = x^n + dt (v - v_gal), v = u/gamma
+ * and the Boris push.
+ *   E[3], B[3]     the forward Yee fields at t^n (read only).
+ *   sp             the forward particles at t^n: x^n, u^{n-1/2} (read only, never permuted).
+ *   Ebar[3], Bbar[3], rhobar   in: adjoints of E^{n+1}, B^{n+1} (Yee) and rho^{n+1} (nodal);
+ *                  out: adjoints of E^n, B^n and rho^n.
+ *   spbar          per species, in: adjoints of x^{n+1}, u^{n+1/2}; out: of x^n, u^{n-1/2}.
+ * The caller keeps checkpoints of the forward state and recomputes each step's
+ * state before reversing it (pic_step must then run with sort_interval = 0 so
+ * that particle order is stable).  Asynchronous.
+ */
+pic_status pic_adjoint_step(pic_ctx* ctx, const double* const E[3], const double* const B[3],
+                            const pic_species* sp, int n_species, double* const Ebar[3], double* const Bbar[3],
+                            double* rhobar, const pic_species_adjoint* spbar);
+
+/*
  * pic_deposit_rho: rho (nodal, overwritten) = sum over species of the direct
  * charge deposition q w S(x - x_i) / dV at the current positions; use it to
  * form rho^0 before the first pic_step.  Asynchronous.

@@ -119,6 +119,7 @@ struct pic_ctx {
   int64_t n_tiles;
   uint32_t* cell_counts;  // FP32 binning: per-cell counts -> offsets, block sums, total
   uint32_t* cell_cursor;  // FP32 binning: per-cell scatter cursors
+  double* adj_work;       // reverse mode: rhobar^n, rhobar^{n+1}, 6 nodal force adjoints
 
   int64_t steps_done;
   // FP32 form: per-species tile ranges of the last binning inside pic_step32
@@ -193,6 +194,12 @@ pic_status psatd_update32(pic_ctx* ctx, float2* EB, float2* J, const float2* rn,
 pic_status psatd_phase32(pic_ctx* ctx, CP6<float2> in, CP6<float2> out, const int* comp_kind, int ncomp, int sign,
                          double scale);
 pic_status psatd_to_nodal32(pic_ctx* ctx, const float2* EB6, float2* G, double scale);
+// Reverse mode (adjoint.cu): conjugate-transposed update on the adjoint spectra in EB (paper
+// convention, in place); G[0..2] = zeta * Jbar / Ncell (nodal DFT), G[3] = rhobar^n / Ncell,
+// G[4] = rhobar^{n+1} / Ncell.
+pic_status psatd_adjoint_update(pic_ctx* ctx, double2* EB, double2* G);
+// EB[c] += zeta_c * src[c] (c = 0..5): transpose of the E, B -> nodal centering.
+pic_status psatd_add_zeta(pic_ctx* ctx, double2* EB, const double2* src);
 
 // particles.cu ----------------------------------------------------------------
 pic_status particles_push(pic_ctx* ctx, const double* const En[3], const double* const Bn[3],

@@ -368,6 +368,84 @@ __host__ __device__ __forceinline__ int stag_mask(int kind) {
   }
 }
 
+// Conjugate transpose of the update (reverse mode).  Per mode, with K v = [k] x v:
+//   Ebar = TC* Ebar' - i TS* K Bbar',  Bbar = TC* Bbar' + i c^2 TS* K Ebar',
+//   Jbar = i X1* K Bbar' + X4* Ebar',  rhobar^n = -i TX3* k.Ebar',  rhobar^{n+1} = i X2* k.Ebar'.
+// EB holds the adjoint spectra (paper convention) in and Ebar, Bbar out; G receives the nodal
+// DFTs of Jbar (times zeta, the transpose of the J centering), rhobar^n and rhobar^{n+1}, / Ncell.
+struct AdjUpdArgs {
+  double2* EB;
+  double2* G;
+  const double2* coef;
+  const double* ks[3];
+  const double* zt[3];
+  int64_t Ny, nzh, nmode;
+  double c2, gscale;
+};
+
+__global__ void __launch_bounds__(256) adjoint_update_kernel(AdjUpdArgs u) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= u.nmode) return;
+  const int64_t nm = u.nmode;
+  const int64_t iz = m % u.nzh, r = m / u.nzh;
+  const int64_t iy = r % u.Ny, ix = r / u.Ny;
+  const double k[3] = {u.ks[0][ix], u.ks[1][iy], u.ks[2][iz]};
+  const double zx = u.zt[0][ix], zy = u.zt[1][iy], zz = u.zt[2][iz];
+  double2 E[3], B[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    E[a] = u.EB[a * nm + m];
+    B[a] = u.EB[(3 + a) * nm + m];
+  }
+  auto cross = [&](const double2* F, double2* o) {
+    o[0] = csub(cscale(F[2], k[1]), cscale(F[1], k[2]));
+    o[1] = csub(cscale(F[0], k[2]), cscale(F[2], k[0]));
+    o[2] = csub(cscale(F[1], k[0]), cscale(F[0], k[1]));
+  };
+  double2 KE[3], KB[3];
+  cross(E, KE);
+  cross(B, KB);
+  auto co = [&](int idx) { return cconj(__ldg(u.coef + idx * nm + m)); };
+  const double2 TC = co(COEF_TC), TS = co(COEF_TS), X1 = co(COEF_X1), X2 = co(COEF_X2), TX3 = co(COEF_TX3),
+                X4 = co(COEF_X4);
+  const double2 kE = cadd(cadd(cscale(E[0], k[0]), cscale(E[1], k[1])), cscale(E[2], k[2]));
+  const double s = u.gscale;
+  const double zj[3] = {zx, zy, zz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2 Eo = csub(cmul(TC, E[a]), cmuli(cmul(TS, KB[a])));
+    const double2 Bo = cadd(cmul(TC, B[a]), cmuli(cscale(cmul(TS, KE[a]), u.c2)));
+    const double2 Jo = cadd(cmuli(cmul(X1, KB[a])), cmul(X4, E[a]));
+    u.EB[a * nm + m] = Eo;
+    u.EB[(3 + a) * nm + m] = Bo;
+    u.G[a * nm + m] = cscale(Jo, zj[a] * s);
+  }
+  u.G[3 * nm + m] = cscale(cmuli(cmul(TX3, kE)), -s);
+  u.G[4 * nm + m] = cscale(cmuli(cmul(X2, kE)), s);
+}
+
+// EB[c] += zeta_c * src[c]: adds the transpose of the E, B -> nodal centering (nodal DFTs in src).
+struct AddZetaArgs {
+  double2* EB;
+  const double2* src;
+  const double* zt[3];
+  int64_t Ny, nzh, nmode;
+};
+
+__global__ void add_zeta_kernel(AddZetaArgs a) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= a.nmode) return;
+  const int c = blockIdx.y;
+  const int64_t iz = m % a.nzh, r = m / a.nzh;
+  const int64_t iy = r % a.Ny, ix = r / a.Ny;
+  const int mk = stag_mask(c);
+  double z = 1.0;
+  if (mk & 1) z *= a.zt[0][ix];
+  if (mk & 2) z *= a.zt[1][iy];
+  if (mk & 4) z *= a.zt[2][iz];
+  a.EB[c * a.nmode + m] = cadd(a.EB[c * a.nmode + m], cscale(a.src[c * a.nmode + m], z));
+}
+
 template <class C>
 struct PhaseArgs {
   CP6<C> in, out;
@@ -658,4 +736,39 @@ pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale) {
 
 pic_status psatd_to_nodal32(pic_ctx* ctx, const float2* EB6, float2* G, double scale) {
   return psatd_to_nodal_t<float2>(ctx, EB6, G, scale);
+}
+
+pic_status psatd_adjoint_update(pic_ctx* ctx, double2* EB, double2* G) {
+  AdjUpdArgs u;
+  u.EB = EB;
+  u.G = G;
+  u.coef = ctx->coef;
+  for (int a = 0; a < 3; ++a) {
+    u.ks[a] = ctx->ks[a];
+    u.zt[a] = ctx->zeta[a];
+  }
+  u.Ny = ctx->N[1];
+  u.nzh = ctx->nzh;
+  u.nmode = ctx->nmode;
+  u.c2 = ctx->c * ctx->c;
+  u.gscale = 1.0 / (double)ctx->ncell;
+  const int bs = 256;
+  adjoint_update_kernel<<<(unsigned)((ctx->nmode + bs - 1) / bs), bs, 0, ctx->stream>>>(u);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
+
+pic_status psatd_add_zeta(pic_ctx* ctx, double2* EB, const double2* src) {
+  AddZetaArgs a;
+  a.EB = EB;
+  a.src = src;
+  for (int k = 0; k < 3; ++k) a.zt[k] = ctx->zeta[k];
+  a.Ny = ctx->N[1];
+  a.nzh = ctx->nzh;
+  a.nmode = ctx->nmode;
+  const int bs = 256;
+  dim3 grid((unsigned)((ctx->nmode + bs - 1) / bs), 6);
+  add_zeta_kernel<<<grid, bs, 0, ctx->stream>>>(a);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
 }

@@ -43,6 +43,10 @@ class PicSpecies32(ctypes.Structure):
                 ("w", _vp), ("id", _vp)]
 
 
+class PicSpeciesAdjoint(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", _vp), ("y", _vp), ("z", _vp), ("ux", _vp), ("uy", _vp), ("uz", _vp)]
+
+
 class PicError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS.get(status, status), msg))
@@ -87,6 +91,8 @@ def _load():
         "pic_field_energy32": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(ctypes.c_int64), P(ctypes.c_int64),
                                               P(ctypes.c_double)]),
         "pic_total_charge32": (ctypes.c_int, [_vp, _vp, P(ctypes.c_double)]),
+        "pic_adjoint_step": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(PicSpecies), ctypes.c_int, P(_vp), P(_vp), _vp,
+                                            P(PicSpeciesAdjoint)]),
         "pic_timing_read": (ctypes.c_int, [_vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
@@ -102,7 +108,8 @@ EXPORTS = ("pic_ext_default", "pic_init", "pic_destroy", "pic_last_error", "pic_
            "pic_center_to_yee", "pic_fft_forward", "pic_fft_inverse", "pic_maxwell_step",
            "pic_coefficient", "pic_field_energy", "pic_total_charge", "pic_timing", "pic_timing_read",
            "pic_center_to_nodal_static", "pic_step32", "pic_deposit_rho32", "pic_push_deposit32", "pic_bin32",
-           "pic_fft_forward32", "pic_fft_inverse32", "pic_field_energy32", "pic_total_charge32")
+           "pic_fft_forward32", "pic_fft_inverse32", "pic_field_energy32", "pic_total_charge32",
+           "pic_adjoint_step")
 
 
 def _ptr(t, n=None):
@@ -232,6 +239,7 @@ class Context:
         self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
         self.nmode = self.shape[0] * self.shape[1] * (self.shape[2] // 2 + 1)
         self.variant = variant
+        self.sort_interval = sort_interval
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ext = PicExt()
         LIB.pic_ext_default(ctypes.byref(ext))
@@ -369,3 +377,13 @@ class Context:
         out = ctypes.c_double()
         self._check(LIB.pic_total_charge32(self.h, _ptr(rho, self.ncell), ctypes.byref(out)))
         return out.value
+
+    # ---- reverse mode ----
+    def adjoint_step(self, E, B, species, Ebar, Bbar, rhobar, species_bar):
+        """pic_adjoint_step: species_bar is a list of dicts with tensors x, y, z, ux, uy, uz."""
+        n = self.ncell
+        arr = (PicSpeciesAdjoint * max(1, len(species_bar)))()
+        for i, (s, b) in enumerate(zip(species, species_bar)):
+            arr[i] = PicSpeciesAdjoint(s.n, *[_ptr(b[k], s.n) for k in ("x", "y", "z", "ux", "uy", "uz")])
+        self._check(LIB.pic_adjoint_step(self.h, _parr(E, n), _parr(B, n), _species_array(species), len(species),
+                                         _parr(Ebar, n), _parr(Bbar, n), _ptr(rhobar, n), arr))

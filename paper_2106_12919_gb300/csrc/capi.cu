@@ -123,7 +123,8 @@ void pic_ext_default(pic_ext* e) {
   e->precision = PIC_FP64;
   e->c = 1.0;
   e->eps0 = 1.0;
-  e->tile[0] = e->tile[1] = e->tile[2] = 8;
+  e->tile[0] = 4;
+  e->tile[1] = e->tile[2] = 8;
   e->sort_interval = 20;
   e->cuda_stream = nullptr;
 }
@@ -132,7 +133,8 @@ void pic_destroy(pic_ctx* ctx) {
   if (!ctx) return;
   void* ptrs[] = {ctx->k1d, ctx->twid[0], ctx->twid[1], ctx->twid[2], ctx->coef, ctx->EBh,
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
-                  ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work};
+                  ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work, ctx->bin_gate,
+                  ctx->bin_outside};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q)

@@ -212,28 +212,38 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   float* jn = Jn(ctx);
   float* Jnp[3] = {jn, jn + nc, jn + 2 * nc};
   const bool tiled = ctx->sort_interval > 0 && tiled_push_fits(ctx);
+  int64_t total = 0;
+  for (int q = 0; q < n_species; ++q) total += sp[q].n;
+  if (tiled && !ctx->bin_gate) {
+    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_gate, sizeof(int)));
+    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_outside, sizeof(unsigned long long)));
+    PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->bin_outside, 0, sizeof(unsigned long long), ctx->stream));
+  }
+  int since_forced = 0;
   for (int s = 0; s < nsteps; ++s) {
     const bool last = s == nsteps - 1;
-    // bin at the first step of every call (the caller may have changed the particles) and then
-    // every sort_interval steps; the tiled push uses the ranges of the species' last binning
-    if (ctx->sort_interval > 0 && (s == 0 || ctx->steps_done % ctx->sort_interval == 0))
-      for (int q = 0; q < n_species; ++q) {
-        StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 3 : 1);
-        int64_t* off = nullptr;
-        if (tiled && q < PIC_MAX_BINNED_SPECIES) {
-          if (!ctx->sp_off[q]) {
-            PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
-          }
-          off = ctx->sp_off[q];
-          ctx->sp_off_n[q] = sp[q].n;
-        }
-        PIC_TRY32(particles_bin32(ctx, &sp[q], off));
+    // Binning: the tiled push needs each species' tile ranges.  The first step of a call and
+    // every sort_interval-th step re-bin unconditionally; in between, the device re-bins only
+    // when more than 2 % of the particles left their tile window in the previous push.
+    if (tiled) {
+      const int force = (s == 0 || since_forced >= ctx->sort_interval) ? 1 : 0;
+      since_forced = force ? 1 : since_forced + 1;
+      {
+        StageScope t(ctx, STAGE_BIN, 1);
+        PIC_TRY32(particles_bin32_decide(ctx, total, force));
       }
+      for (int q = 0; q < n_species && q < PIC_MAX_BINNED_SPECIES; ++q) {
+        StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 8 : 4);
+        if (!ctx->sp_off[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
+        ctx->sp_off_n[q] = sp[q].n;
+        PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate));
+      }
+    }
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(jn, 0, 3 * nc * sizeof(float), ctx->stream));
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(rho, 0, nc * sizeof(float), ctx->stream));
     for (int q = 0; q < n_species; ++q) {
       StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
-      if (tiled && q < PIC_MAX_BINNED_SPECIES && ctx->sp_off[q] && ctx->sp_off_n[q] == sp[q].n)
+      if (tiled && q < PIC_MAX_BINNED_SPECIES)
         PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q]));
       else
         PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));

@@ -114,7 +114,7 @@ struct Window {
 // atomics, outside it (a particle that left its tile since the last binning)
 // with global atomics.  comp0 = 0 deposits (v0, v1, v2) into J, comp0 = 3 deposits r into rho.
 template <int P>
-__device__ __forceinline__ void deposit_window(const Push32Args& a, const Window& win, int ix, int iy, int iz,
+__device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window& win, int ix, int iy, int iz,
                                                float fx, float fy, float fz, float v0, float v1, float v2, float r,
                                                bool j) {
   constexpr int NS = P + 1;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void deposit_window(const Push32Args& a, const Window
   if (!inside) {
     if (j) deposit_node_block<P>(a, ix, iy, iz, fx, fy, fz, v0, v1, v2, 0.f, true);
     else deposit_node_block<P>(a, ix, iy, iz, fx, fy, fz, 0.f, 0.f, 0.f, r, false);
-    return;
+    return false;
   }
   const int plane = win.W[1] * win.W[2];
   const int vol = win.W[0] * plane;
@@ -152,6 +152,7 @@ __device__ __forceinline__ void deposit_window(const Push32Args& a, const Window
       }
     }
   }
+  return true;
 }
 
 template <int P>
@@ -229,6 +230,7 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
 // up to one cell), then flushes the window once with global atomics.
 struct TileArgs {
   const int64_t* off;  // [n_tiles + 1] particle ranges
+  unsigned long long* outside;  // count of particles that used the global-memory path
   int T[3];            // tile edge (cells)
   int nt[3];           // tiles per axis
   int W[3];            // window edge = T + 5
@@ -239,7 +241,7 @@ struct TileArgs {
 // 8-byte shared loads per node; a particle whose gather block is outside the
 // staged nodes (it left the tile since the last binning) gathers from global memory.
 template <int P>
-__global__ void __launch_bounds__(256, 3) push32_tile_kernel(Push32Args a, TileArgs t) {
+__global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileArgs t) {
   extern __shared__ float smem[];
   const int tile = blockIdx.x;
   const int tz = tile % t.nt[2], ty = (tile / t.nt[2]) % t.nt[1], tx = tile / (t.nt[1] * t.nt[2]);
@@ -267,7 +269,12 @@ __global__ void __launch_bounds__(256, 3) push32_tile_kernel(Push32Args a, TileA
   __syncthreads();
   constexpr int NS = P + 1;
   const int p0 = (int)t.off[tile], p1 = (int)t.off[tile + 1];
-  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+  // particles are cell-sorted; visiting them with a stride of two spreads the particles of one
+  // cell over different warp instructions, so their deposits do not hit the same shared address
+  // in the same instruction
+  const int cnt = p1 - p0, half = (cnt + 1) >> 1;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const int p = p0 + (j < half ? 2 * j : 2 * (j - half) + 1);
     const int c = a.cell[p];
     const int ix = (c >> (a.shz + a.shy)) & a.mask[0], iy = (c >> a.shz) & a.mask[1], iz = c & a.mask[2];
     const float fx = a.fx[p], fy = a.fy[p], fz = a.fz[p];
@@ -279,7 +286,8 @@ __global__ void __launch_bounds__(256, 3) push32_tile_kernel(Push32Args a, TileA
     shape32<P>(iz, fz, lz, Sz);
     float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int gx = lx - go0, gy = ly - go1, gz = lz - go2;
-    if (gx >= 0 && gy >= 0 && gz >= 0 && gx + NS <= G0 && gy + NS <= G1 && gz + NS <= G2) {
+    const bool gin = gx >= 0 && gy >= 0 && gz >= 0 && gx + NS <= G0 && gy + NS <= G1 && gz + NS <= G2;
+    if (gin) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
 #pragma unroll
@@ -344,8 +352,11 @@ __global__ void __launch_bounds__(256, 3) push32_tile_kernel(Push32Args a, TileA
     a.ux[p] = ux;
     a.uy[p] = uy;
     a.uz[p] = uz;
-    deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
-    deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
+    const bool jin = deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
+    const bool rin = deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
+    const unsigned act = __activemask();
+    const unsigned outb = __ballot_sync(act, !(gin && jin && rin));
+    if (outb && (threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(t.outside, (unsigned long long)__popc(outb));
   }
   __syncthreads();
   // flush the window: node (i, j, k) of the window is global node org + (i, j, k), wrapped
@@ -412,6 +423,7 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
   if (a.n == 0) return PIC_OK;
   TileArgs t;
   t.off = off;
+  t.outside = ctx->bin_outside;
   int vol = 1;
   for (int d = 0; d < 3; ++d) {
     t.T[d] = ctx->tile[d];
@@ -442,7 +454,24 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
 // key = tile * cells_per_tile + local cell (z fastest), so particles end up grouped by
 // tile and, inside a tile, ordered by cell (integer only: from the cell index)
 // ---------------------------------------------------------------------------
+// Binning runs only when *gate is non-zero (the device decides, see bin_decide_kernel), so it can
+// be enqueued every step without a host round trip.
+__device__ __forceinline__ bool gated_off(const int* gate) { return gate != nullptr && *gate == 0; }
+
+__global__ void fill_u32_kernel(uint32_t* p, int64_t n, uint32_t v, const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = v;
+}
+
+// gate = (particles outside their tile window in the last push) > limit, or forced; resets the count
+__global__ void bin_decide_kernel(int* gate, unsigned long long* outside, unsigned long long limit, int force) {
+  *gate = (force || *outside > limit) ? 1 : 0;
+  *outside = 0ull;
+}
+
 struct Key32Args {
+  const int* gate;
   const int32_t* cell;
   int64_t n;
   int shz, shy;
@@ -457,6 +486,7 @@ struct Key32Args {
 };
 
 __global__ void key32_kernel(Key32Args a) {
+  if (gated_off(a.gate)) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= a.n) return;
   const int c = a.cell[p];
@@ -474,7 +504,8 @@ __global__ void key32_kernel(Key32Args a) {
 // exclusive scan, phase 1: each block scans 4096 counts in place (to offsets within the block)
 // and writes its total to bsum[block]
 constexpr int kScanBlock = 4096;
-__global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n, uint32_t* bsum) {
+__global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n, uint32_t* bsum, const int* gate) {
+  if (gated_off(gate)) return;
   __shared__ uint32_t part[1024];
   const int64_t base = (int64_t)blockIdx.x * kScanBlock;
   uint32_t x[4];
@@ -504,7 +535,9 @@ __global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n
 }
 
 // phase 2: one CTA scans the block totals (exclusive) and writes the grand total
-__global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* bsum, int64_t nb, uint32_t* total) {
+__global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* bsum, int64_t nb, uint32_t* total,
+                                                         const int* gate) {
+  if (gated_off(gate)) return;
   __shared__ uint32_t part[1024];
   const int64_t chunk = (nb + 1023) / 1024;
   const int64_t b = threadIdx.x * chunk, e = min(nb, b + chunk);
@@ -529,7 +562,8 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* bsum, int64_t
 
 // phase 3: add the block offsets; also emit the per-tile ranges off[t] = cell offset of the tile's first key
 __global__ void scan_add_kernel(uint32_t* v, int64_t n, const uint32_t* bsum, int cpt_shift, int64_t* tile_off,
-                                int64_t n_tiles, const uint32_t* total) {
+                                int64_t n_tiles, const uint32_t* total, const int* gate) {
+  if (gated_off(gate)) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
     const uint32_t o = v[i] + bsum[i / kScanBlock];
@@ -540,6 +574,7 @@ __global__ void scan_add_kernel(uint32_t* v, int64_t n, const uint32_t* bsum, in
 }
 
 struct Scatter32Args {
+  const int* gate;
   const uint32_t* src[8];  // cell, fx, fy, fz, ux, uy, uz, w as 32-bit words
   uint32_t* dst[8];
   const unsigned long long* id_src;
@@ -551,6 +586,7 @@ struct Scatter32Args {
 };
 
 __global__ void scatter32_kernel(Scatter32Args a) {
+  if (gated_off(a.gate)) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= a.n) return;
   const int k = a.key[p];
@@ -568,7 +604,33 @@ __global__ void scatter32_kernel(Scatter32Args a) {
   if (a.id_src) a.id_dst[q] = a.id_src[p];
 }
 
+// copy the sorted scratch back into the species arrays (8 words + optional id per particle)
+struct CopyBackArgs {
+  const int* gate;
+  const uint32_t* src[8];
+  uint32_t* dst[8];
+  const unsigned long long* id_src;
+  unsigned long long* id_dst;
+  int64_t n;
+};
+
+__global__ void copy_back_kernel(CopyBackArgs a) {
+  if (gated_off(a.gate)) return;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int f = 0; f < 8; ++f) a.dst[f][p] = a.src[f][p];
+    if (a.id_src) a.id_dst[p] = a.id_src[p];
+  }
+}
+
 }  // namespace
+
+pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force) {
+  const unsigned long long limit = (unsigned long long)(0.02 * (double)total_particles);
+  bin_decide_kernel<<<1, 1, 0, ctx->stream>>>(ctx->bin_gate, ctx->bin_outside, limit, force);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
 
 pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                             const pic_species32* sp, float* const J[3], float* rho) {
@@ -614,7 +676,7 @@ pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float*
   return launch_push32(ctx, a);
 }
 
-pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out) {
+pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate) {
   const int64_t n = sp->n;
   pic_status st = particles_bin_capacity(ctx, n > 0 ? n : 1);
   if (st != PIC_OK) return st;
@@ -627,8 +689,11 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   uint32_t* counts = ctx->cell_counts;
   uint32_t* bsum = counts + ncell;
   uint32_t* total = bsum + nblk;
-  PIC_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, ncell * sizeof(uint32_t), ctx->stream));
+  const unsigned fill_blocks = 152 * 8;
+  fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(counts, ncell, 0u, gate);
+  PIC_LAUNCH_CHECK(ctx);
   Key32Args b;
+  b.gate = gate;
   b.cell = sp->cell;
   b.n = n;
   b.shz = ilog2(ctx->N[2]);
@@ -651,18 +716,20 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
     key32_kernel<<<nb, bs, 0, ctx->stream>>>(b);
     PIC_LAUNCH_CHECK(ctx);
   }
-  scan_block_kernel<<<(unsigned)nblk, 1024, 0, ctx->stream>>>(counts, ncell, bsum);
+  scan_block_kernel<<<(unsigned)nblk, 1024, 0, ctx->stream>>>(counts, ncell, bsum, gate);
   PIC_LAUNCH_CHECK(ctx);
-  scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(bsum, nblk, total);
+  scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(bsum, nblk, total, gate);
   PIC_LAUNCH_CHECK(ctx);
   int64_t* tile_off = offsets_out ? offsets_out : ctx->bin_counts;
   scan_add_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, ctx->stream>>>(counts, ncell, bsum, b.cpt_shift,
-                                                                           tile_off, ctx->n_tiles, total);
+                                                                           tile_off, ctx->n_tiles, total, gate);
   PIC_LAUNCH_CHECK(ctx);
   if (n == 0) return PIC_OK;
   if (!ctx->cell_cursor) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->cell_cursor, ncell * sizeof(uint32_t)));
-  PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_cursor, 0, ncell * sizeof(uint32_t), ctx->stream));
+  fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(ctx->cell_cursor, ncell, 0u, gate);
+  PIC_LAUNCH_CHECK(ctx);
   Scatter32Args s;
+  s.gate = gate;
   void* fields[8] = {sp->cell, sp->fx, sp->fy, sp->fz, sp->ux, sp->uy, sp->uz, sp->w};
   uint32_t* tmp = reinterpret_cast<uint32_t*>(ctx->bin_tmp);
   for (int f = 0; f < 8; ++f) {
@@ -677,10 +744,16 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   s.cursor = ctx->cell_cursor;
   scatter32_kernel<<<nb, bs, 0, ctx->stream>>>(s);
   PIC_LAUNCH_CHECK(ctx);
-  for (int f = 0; f < 8; ++f)
-    PIC_CUDA_TRY(ctx, cudaMemcpyAsync(fields[f], s.dst[f], n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
-                                      ctx->stream));
-  if (sp->id)
-    PIC_CUDA_TRY(ctx, cudaMemcpyAsync(sp->id, s.id_dst, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+  CopyBackArgs cb;
+  cb.gate = gate;
+  for (int f = 0; f < 8; ++f) {
+    cb.src[f] = s.dst[f];
+    cb.dst[f] = static_cast<uint32_t*>(fields[f]);
+  }
+  cb.id_src = sp->id ? s.id_dst : nullptr;
+  cb.id_dst = reinterpret_cast<unsigned long long*>(sp->id);
+  cb.n = n;
+  copy_back_kernel<<<152 * 8, 256, 0, ctx->stream>>>(cb);
+  PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }

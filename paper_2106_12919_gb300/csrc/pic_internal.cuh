@@ -120,6 +120,8 @@ struct pic_ctx {
   uint32_t* cell_counts;  // FP32 binning: per-cell counts -> offsets, block sums, total
   uint32_t* cell_cursor;  // FP32 binning: per-cell scatter cursors
   double* adj_work;       // reverse mode: rhobar^n, rhobar^{n+1}, 6 nodal force adjoints
+  int* bin_gate;                    // FP32 form: device flag "re-bin before the next push"
+  unsigned long long* bin_outside;  // FP32 form: particles that left their tile window in the last push
 
   int64_t steps_done;
   // FP32 form: per-species tile ranges of the last binning inside pic_step32
@@ -216,7 +218,10 @@ pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float*
 bool tiled_push_fits(const pic_ctx* ctx);  // deposit window of the tile fits in shared memory
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                                   const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets);
-pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out);
+// gate: device flag; the binning kernels do nothing while *gate == 0 (nullptr = always bin)
+pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate = nullptr);
+// *bin_gate = (particles outside their tile window in the last tiled push > 2 % of total) || force
+pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force);
 
 // center.cu -------------------------------------------------------------------
 pic_status center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);

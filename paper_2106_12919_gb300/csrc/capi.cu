@@ -137,8 +137,10 @@ void pic_destroy(pic_ctx* ctx) {
                   ctx->bin_outside};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q)
+  for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) {
     if (ctx->sp_off[q]) cudaFree(ctx->sp_off[q]);
+    if (ctx->sp_chunk[q]) cudaFree(ctx->sp_chunk[q]);
+  }
   timers_free(ctx);
   delete ctx;
 }

@@ -233,10 +233,11 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
         PIC_TRY32(particles_bin32_decide(ctx, total, force));
       }
       for (int q = 0; q < n_species && q < PIC_MAX_BINNED_SPECIES; ++q) {
-        StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 8 : 4);
+        StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 12 : 8);
         if (!ctx->sp_off[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
+        if (!ctx->sp_chunk[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_chunk[q], tile_chunk_words(ctx) * sizeof(uint32_t)));
         ctx->sp_off_n[q] = sp[q].n;
-        PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate));
+        PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q]));
       }
     }
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(jn, 0, 3 * nc * sizeof(float), ctx->stream));
@@ -244,7 +245,7 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     for (int q = 0; q < n_species; ++q) {
       StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
       if (tiled && q < PIC_MAX_BINNED_SPECIES)
-        PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q]));
+        PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q], ctx->sp_chunk[q]));
       else
         PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
     }

@@ -224,12 +224,16 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
   deposit_node_block<P>(a, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
 }
 
-// Tiled form: one CTA per particle tile (ranges from the last binning).  Gathers
-// through L1, accumulates J and rho in a shared-memory window covering the tile
-// plus two guard cells on each side (enough for a cubic shape and a move of
-// up to one cell), then flushes the window once with global atomics.
+// Tiled form: one CTA per chunk of a particle tile (ranges from the last binning;
+// a tile holding more than kTileChunk particles is split into equal chunks so that
+// a dense bunch spreads over many SMs).  Gathers through L1, accumulates J and rho
+// in a shared-memory window covering the tile plus two guard cells on each side
+// (enough for a cubic shape and a move of up to one cell), then flushes the window
+// once with global atomics.
 struct TileArgs {
-  const int64_t* off;  // [n_tiles + 1] particle ranges
+  const int64_t* off;     // [n_tiles + 1] particle ranges
+  const uint32_t* chunk;  // [n_tiles + 1] exclusive prefix sum of chunks per tile
+  int64_t n_tiles;
   unsigned long long* outside;  // count of particles that used the global-memory path
   int T[3];            // tile edge (cells)
   int nt[3];           // tiles per axis
@@ -243,7 +247,27 @@ struct TileArgs {
 template <int P>
 __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileArgs t) {
   extern __shared__ float smem[];
-  const int tile = blockIdx.x;
+  __shared__ int s_tile, s_part;
+  if (threadIdx.x == 0) {
+    // chunk blockIdx.x belongs to the last tile whose chunk start is <= blockIdx.x
+    const uint32_t b = blockIdx.x;
+    int tl = -1, k = 0;
+    if (b < t.chunk[t.n_tiles]) {
+      int64_t lo = 0, hi = t.n_tiles;  // invariant: chunk[lo] <= b < chunk[hi]
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (t.chunk[mid] <= b) lo = mid;
+        else hi = mid;
+      }
+      tl = (int)lo;
+      k = (int)(b - t.chunk[lo]);
+    }
+    s_tile = tl;
+    s_part = k;
+  }
+  __syncthreads();
+  const int tile = s_tile;
+  if (tile < 0) return;
   const int tz = tile % t.nt[2], ty = (tile / t.nt[2]) % t.nt[1], tx = tile / (t.nt[1] * t.nt[2]);
   Window win;
   win.org[0] = tx * t.T[0] - 2;
@@ -268,7 +292,13 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
   }
   __syncthreads();
   constexpr int NS = P + 1;
-  const int p0 = (int)t.off[tile], p1 = (int)t.off[tile + 1];
+  int p0, p1;
+  {
+    const int64_t b0 = t.off[tile], cnt_t = t.off[tile + 1] - b0;
+    const int64_t nch = t.chunk[tile + 1] - t.chunk[tile], k = s_part;
+    p0 = (int)(b0 + cnt_t * k / nch);
+    p1 = (int)(b0 + cnt_t * (k + 1) / nch);
+  }
   // particles are cell-sorted; visiting them with a stride of two spreads the particles of one
   // cell over different warp instructions, so their deposits do not hit the same shared address
   // in the same instruction
@@ -419,10 +449,12 @@ pic_status launch_push32(pic_ctx* ctx, const Push32Args& a) {
   return PIC_OK;
 }
 
-pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t* off) {
+pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t* off, const uint32_t* chunk) {
   if (a.n == 0) return PIC_OK;
   TileArgs t;
   t.off = off;
+  t.chunk = chunk;
+  t.n_tiles = ctx->n_tiles;
   t.outside = ctx->bin_outside;
   int vol = 1;
   for (int d = 0; d < 3; ++d) {
@@ -434,7 +466,8 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
   size_t gvol = 1;
   for (int d = 0; d < 3; ++d) gvol *= (size_t)(ctx->tile[d] + 3);
   const size_t smem = 4 * (size_t)vol * sizeof(float) + 6 * gvol * sizeof(float);
-  const unsigned nb = (unsigned)ctx->n_tiles;
+  // sum over tiles of ceil(count / kTileChunk) < n_tiles + n / kTileChunk: surplus CTAs return at once
+  const unsigned nb = (unsigned)(ctx->n_tiles + (a.n + kTileChunk - 1) / kTileChunk);
   if (smem > 48 * 1024) {
     PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -573,6 +606,21 @@ __global__ void scan_add_kernel(uint32_t* v, int64_t n, const uint32_t* bsum, in
   if (i == 0) tile_off[n_tiles] = (int64_t)*total;
 }
 
+// chunks per tile: nch[t] = ceil(count_t / kTileChunk), scanned in place afterwards
+__global__ void chunk_count_kernel(const int64_t* off, int64_t n_tiles, uint32_t* nch, const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_tiles; i += (int64_t)gridDim.x * blockDim.x)
+    nch[i] = (uint32_t)((off[i + 1] - off[i] + kTileChunk - 1) / kTileChunk);
+}
+
+__global__ void chunk_add_kernel(uint32_t* v, int64_t n, const uint32_t* bsum, const uint32_t* total,
+                                 const int* gate) {
+  if (gated_off(gate)) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v[i] += bsum[i / kScanBlock];
+  if (i == 0) v[n] = *total;
+}
+
 struct Scatter32Args {
   const int* gate;
   const uint32_t* src[8];  // cell, fx, fy, fz, ux, uy, uz, w as 32-bit words
@@ -654,8 +702,14 @@ bool tiled_push_fits(const pic_ctx* ctx) {
   return (4 * vol + 6 * gvol) * sizeof(float) <= 160 * 1024 && ctx->ncell < (int64_t(1) << 31);
 }
 
+size_t tile_chunk_words(const pic_ctx* ctx) {
+  // chunk starts [n_tiles + 1], scan block sums, scan total
+  return (size_t)ctx->n_tiles + 1 + (size_t)((ctx->n_tiles + kScanBlock - 1) / kScanBlock) + 1;
+}
+
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
-                                  const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets) {
+                                  const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets,
+                                  const uint32_t* chunks) {
   Push32Args a = make_args32(ctx, sp);
   for (int c = 0; c < 3; ++c) {
     a.F[c] = En[c];
@@ -664,7 +718,7 @@ pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const 
   }
   a.rho = rho;
   a.gather = 1;
-  return launch_push32_tiled(ctx, a, offsets);
+  return launch_push32_tiled(ctx, a, offsets, chunks);
 }
 
 pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float* rho) {
@@ -676,7 +730,8 @@ pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float*
   return launch_push32(ctx, a);
 }
 
-pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate) {
+pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate,
+                           uint32_t* chunks_out) {
   const int64_t n = sp->n;
   pic_status st = particles_bin_capacity(ctx, n > 0 ? n : 1);
   if (st != PIC_OK) return st;
@@ -724,6 +779,20 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   scan_add_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, ctx->stream>>>(counts, ncell, bsum, b.cpt_shift,
                                                                            tile_off, ctx->n_tiles, total, gate);
   PIC_LAUNCH_CHECK(ctx);
+  if (chunks_out) {
+    const int64_t nt = ctx->n_tiles;
+    const int64_t nblk_t = (nt + kScanBlock - 1) / kScanBlock;
+    uint32_t* cbsum = chunks_out + nt + 1;
+    uint32_t* ctotal = cbsum + nblk_t;
+    chunk_count_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(tile_off, nt, chunks_out, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    scan_block_kernel<<<(unsigned)nblk_t, 1024, 0, ctx->stream>>>(chunks_out, nt, cbsum, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(cbsum, nblk_t, ctotal, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    chunk_add_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(chunks_out, nt, cbsum, ctotal, gate);
+    PIC_LAUNCH_CHECK(ctx);
+  }
   if (n == 0) return PIC_OK;
   if (!ctx->cell_cursor) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->cell_cursor, ncell * sizeof(uint32_t)));
   fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(ctx->cell_cursor, ncell, 0u, gate);

@@ -127,6 +127,7 @@ struct pic_ctx {
   // FP32 form: per-species tile ranges of the last binning inside pic_step32
   int64_t* sp_off[PIC_MAX_BINNED_SPECIES];
   int64_t sp_off_n[PIC_MAX_BINNED_SPECIES];   // particle count they were built for, -1 = invalid
+  uint32_t* sp_chunk[PIC_MAX_BINNED_SPECIES];  // per-species chunk starts of the tiled push (see below)
   Timers timers;
   char err[256];
 };
@@ -213,13 +214,20 @@ pic_status particles_bin_capacity(pic_ctx* ctx, int64_t n);
 pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                             const pic_species32* sp, float* const J[3], float* rho);
 pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float* rho);
-// Tiled push: one CTA per tile over the ranges offsets[n_tiles + 1] of the last binning,
-// shared-memory deposit window per tile.  Correct for any order (out-of-window deposits go global).
+// Tiled push: one CTA per chunk of at most kTileChunk particles of one tile, over the ranges
+// offsets[n_tiles + 1] of the last binning; chunks[n_tiles + 1] holds the exclusive prefix sum
+// of the tiles' chunk counts.  Shared-memory deposit window per chunk.  Correct for any order
+// (out-of-window deposits go global).
+constexpr int kTileChunk = 2048;
 bool tiled_push_fits(const pic_ctx* ctx);  // deposit window of the tile fits in shared memory
+size_t tile_chunk_words(const pic_ctx* ctx);  // size of a chunks array incl. its scan scratch
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
-                                  const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets);
-// gate: device flag; the binning kernels do nothing while *gate == 0 (nullptr = always bin)
-pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate = nullptr);
+                                  const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets,
+                                  const uint32_t* chunks);
+// gate: device flag; the binning kernels do nothing while *gate == 0 (nullptr = always bin).
+// chunks_out (optional, tile_chunk_words entries): chunk starts for particles_push32_tiled.
+pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate = nullptr,
+                           uint32_t* chunks_out = nullptr);
 // *bin_gate = (particles outside their tile window in the last tiled push > 2 % of total) || force
 pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force);
 

@@ -147,6 +147,9 @@ def test_bin32_offsets_exact():
 CASES = [
     ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 100, False),
     ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 100, False),
+    # a dense driver: its central tiles hold up to ~5000 particles, so the tiled push
+    # splits them into chunks of at most 2048 that deposit into the same tile window
+    ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=100000), 20, False),
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 100, True),
     ("galilean_drift", dict(shape=(16, 16, 32), ppc=1), 100, True),
 ]

@@ -163,6 +163,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--form", default="both", choices=["both", "fp32", "fp64"],
                     help="both: FP32 form timed as the headline, FP64 form beside it")
+    ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="run the workload's generator on a smaller box (same dx, dt, physics), e.g. for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -183,7 +185,7 @@ def main():
     __graft_entry__.build()
 
 
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, tuple(args.grid) if args.grid else None)
     p = w["params"]
     shape = p["shape"]
     ncell = shape[0] * shape[1] * shape[2]
@@ -325,7 +327,7 @@ def run_form(form, w, args, world, rank, local):
         # 32 B read + 28 B written per particle; nodal E, B read (24 B) and J, rho deposited (16 B) per cell
         nbytes = 60 * per_launch + 40 * ncell
         achieved = nbytes / push_avg_s / 1e9
-        roofline = {"kernel": "push32_kernel (gather + Boris + deposit)", "bound": "hbm", "achieved": achieved,
+        roofline = {"kernel": "push32_tile_kernel (gather + Boris + deposit)", "bound": "hbm", "achieved": achieved,
                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                     "algorithmic_bytes": "60 B/particle + 40 B/cell per launch"}
     else:

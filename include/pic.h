@@ -336,7 +336,9 @@ pic_status pic_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, int n_specie
 pic_status pic_push_deposit32(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                               const pic_species32* sp, int n_species, float* const J_nodal[3], float* rho_nodal);
 
-/* pic_bin32: pic_bin in the FP32 form (tile from the integer cell index). */
+/* pic_bin32: pic_bin in the FP32 form (tile from the integer cell index).  Inside a tile the
+ * particles come out ordered by cell, z fastest, then x, then y (the order the tiled push's
+ * shared-memory layout is built for); the order among particles of one cell is unspecified. */
 pic_status pic_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets);
 
 /* pic_fft_forward32 / pic_fft_inverse32: pic_fft_forward / inverse on float arrays

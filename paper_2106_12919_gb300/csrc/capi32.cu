@@ -233,9 +233,14 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
         PIC_TRY32(particles_bin32_decide(ctx, total, force));
       }
       for (int q = 0; q < n_species && q < PIC_MAX_BINNED_SPECIES; ++q) {
-        StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 12 : 8);
+        StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 13 : 9);
         if (!ctx->sp_off[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
-        if (!ctx->sp_chunk[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_chunk[q], tile_chunk_words(ctx) * sizeof(uint32_t)));
+        if (!ctx->sp_chunk[q] || ctx->sp_chunk_n[q] < sp[q].n) {
+          if (ctx->sp_chunk[q]) PIC_CUDA_TRY(ctx, cudaFree(ctx->sp_chunk[q]));
+          ctx->sp_chunk[q] = nullptr;
+          PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_chunk[q], tile_chunk_words(ctx, sp[q].n) * sizeof(uint32_t)));
+          ctx->sp_chunk_n[q] = sp[q].n;
+        }
         ctx->sp_off_n[q] = sp[q].n;
         PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q]));
       }

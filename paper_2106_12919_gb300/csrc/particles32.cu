@@ -103,16 +103,18 @@ __device__ __forceinline__ void deposit_node_block(const Push32Args& a, int ix, 
 }
 
 // Shared-memory deposit window of one tile: nodes [org, org + W) per axis
-// (unwrapped coordinates), four FP32 components (J^x, J^y, J^z, rho).
+// (unwrapped coordinates), four FP32 components (J^x, J^y, J^z, rho), each
+// [W0][W1][W2] with row stride W2 and plane stride `plane` (padded, see TileArgs).
 struct Window {
-  float* acc;     // [4][W0][W1][W2]
+  float* acc;
   int org[3];
   int W[3];
+  int plane, comp;
 };
 
 // Deposit one particle's (P+1)^3 block: inside the window with shared-memory
 // atomics, outside it (a particle that left its tile since the last binning)
-// with global atomics.  comp0 = 0 deposits (v0, v1, v2) into J, comp0 = 3 deposits r into rho.
+// with global atomics.  j: (v0, v1, v2) into J, else r into rho.
 template <int P>
 __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window& win, int ix, int iy, int iz,
                                                float fx, float fy, float fz, float v0, float v1, float v2, float r,
@@ -131,23 +133,22 @@ __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window
     else deposit_node_block<P>(a, ix, iy, iz, fx, fy, fz, 0.f, 0.f, 0.f, r, false);
     return false;
   }
-  const int plane = win.W[1] * win.W[2];
-  const int vol = win.W[0] * plane;
+  const int comp = win.comp;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
 #pragma unroll
     for (int jj = 0; jj < NS; ++jj) {
       const float sxy = Sx[i] * Sy[jj];
-      float* row = win.acc + (wx + i) * plane + (wy + jj) * win.W[2] + wz;
+      float* row = win.acc + (wx + i) * win.plane + (wy + jj) * win.W[2] + wz;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         const float s = sxy * Sz[k];
         if (j) {
           atomicAdd(row + k, s * v0);
-          atomicAdd(row + vol + k, s * v1);
-          atomicAdd(row + 2 * vol + k, s * v2);
+          atomicAdd(row + comp + k, s * v1);
+          atomicAdd(row + 2 * comp + k, s * v2);
         } else {
-          atomicAdd(row + 3 * vol + k, s * r);
+          atomicAdd(row + 3 * comp + k, s * r);
         }
       }
     }
@@ -226,41 +227,49 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
 
 // Tiled form: one CTA per chunk of a particle tile (ranges from the last binning;
 // a tile holding more than kTileChunk particles is split into equal chunks so that
-// a dense bunch spreads over many SMs).  Gathers through L1, accumulates J and rho
-// in a shared-memory window covering the tile plus two guard cells on each side
-// (enough for a cubic shape and a move of up to one cell), then flushes the window
-// once with global atomics.
+// a dense bunch spreads over many SMs).  The tile's nodal E, B plus guard nodes are
+// staged in shared memory, J and rho accumulate in a shared-memory window covering
+// the tile plus two guard cells on each side (enough for a cubic shape and a move of
+// up to one cell), and the window is flushed once with global atomics.
+//
+// Shared-memory layout.  Binning orders the cells of a tile z fastest, then x, then y,
+// so at P particles per cell the 32 lanes of a warp (visiting every P-th particle)
+// hold 32 cells: all T2 = 8 z-cells of T0 = 4 x-planes at one y.  Both shared arrays
+// are component-planar with the plane stride padded to 8 (mod 32) words, so the
+// lanes' addresses for the same relative node fall in 32 distinct banks: every
+// gather load and every deposit atomic of such a warp is one conflict-free access.
 struct TileArgs {
   const int64_t* off;     // [n_tiles + 1] particle ranges
   const uint32_t* chunk;  // [n_tiles + 1] exclusive prefix sum of chunks per tile
+  const uint32_t* chunk_tile;  // tile of each chunk
   int64_t n_tiles;
   unsigned long long* outside;  // count of particles that used the global-memory path
-  int T[3];            // tile edge (cells)
-  int nt[3];           // tiles per axis
-  int W[3];            // window edge = T + 5
+  int T[3];               // tile edge (cells)
+  int nt[3];              // tiles per axis
+  int cpt;                // cells per tile
+  int W[3];               // deposit window edge = T + 5
+  int wplane, wcomp;      // deposit window plane and component strides (words)
+  int G[3];               // gather window edge = T + 3: nodes [T0 - 1, T0 + T + 2)
+  int gplane, gcomp;      // gather window plane and component strides (words)
 };
 
-// The tile's nodal E, B (nodes [T0 - 1, T0 + T + 2) per axis) are staged once in
-// shared memory as 6-float records, so the gather of a fresh particle is three
-// 8-byte shared loads per node; a particle whose gather block is outside the
-// staged nodes (it left the tile since the last binning) gathers from global memory.
+// particle of a chunk visited by slot j when every s-th particle goes to consecutive slots
+__device__ __forceinline__ int interleaved(int j, int q, int s) {
+  const int r = j / q;
+  return (j - r * q) * s + r;
+}
+
 template <int P>
 __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileArgs t) {
   extern __shared__ float smem[];
   __shared__ int s_tile, s_part;
   if (threadIdx.x == 0) {
-    // chunk blockIdx.x belongs to the last tile whose chunk start is <= blockIdx.x
+    // chunk blockIdx.x: its tile from the chunk map, its index within the tile from the chunk starts
     const uint32_t b = blockIdx.x;
     int tl = -1, k = 0;
     if (b < t.chunk[t.n_tiles]) {
-      int64_t lo = 0, hi = t.n_tiles;  // invariant: chunk[lo] <= b < chunk[hi]
-      while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (t.chunk[mid] <= b) lo = mid;
-        else hi = mid;
-      }
-      tl = (int)lo;
-      k = (int)(b - t.chunk[lo]);
+      tl = (int)t.chunk_tile[b];
+      k = (int)(b - t.chunk[tl]);
     }
     s_tile = tl;
     s_part = k;
@@ -274,37 +283,39 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
   win.org[1] = ty * t.T[1] - 2;
   win.org[2] = tz * t.T[2] - 2;
   for (int d = 0; d < 3; ++d) win.W[d] = t.W[d];
-  const int vol = t.W[0] * t.W[1] * t.W[2];
+  win.plane = t.wplane;
+  win.comp = t.wcomp;
   win.acc = smem;
-  // gather window: nodes [T0 - 1, T0 + T + 2), i.e. G = T + 3 per axis, record of 6 floats (+ pad to 6)
-  const int G0 = t.T[0] + 3, G1 = t.T[1] + 3, G2 = t.T[2] + 3;
-  const int gvol = G0 * G1 * G2;
-  float2* fld = reinterpret_cast<float2*>(smem + 4 * vol);  // [gvol][3] float2
+  const int G1 = t.G[1], G2 = t.G[2], gplane = t.gplane, gcomp = t.gcomp;
+  float* fld = smem + 4 * t.wcomp;  // [6][G0][G1][G2], plane stride gplane
   const int go0 = tx * t.T[0] - 1, go1 = ty * t.T[1] - 1, go2 = tz * t.T[2] - 1;
-  for (int e = threadIdx.x; e < 4 * vol; e += blockDim.x) smem[e] = 0.0f;
+  for (int e = threadIdx.x; e < 4 * t.wcomp; e += blockDim.x) smem[e] = 0.0f;
+  const int gvol = t.G[0] * G1 * G2;
   for (int e = threadIdx.x; e < gvol; e += blockDim.x) {
     const int k = e % G2, r = e / G2;
     const int j = r % G1, i = r / G1;
     const int o = (((go0 + i) & a.mask[0]) * (int)a.Ny + ((go1 + j) & a.mask[1])) * (int)a.Nz + ((go2 + k) & a.mask[2]);
-    fld[3 * e + 0] = make_float2(__ldg(a.F[0] + o), __ldg(a.F[1] + o));
-    fld[3 * e + 1] = make_float2(__ldg(a.F[2] + o), __ldg(a.F[3] + o));
-    fld[3 * e + 2] = make_float2(__ldg(a.F[4] + o), __ldg(a.F[5] + o));
+    const int d = i * gplane + j * G2 + k;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) fld[q * gcomp + d] = __ldg(a.F[q] + o);
   }
   __syncthreads();
   constexpr int NS = P + 1;
-  int p0, p1;
+  int p0, cnt;
   {
     const int64_t b0 = t.off[tile], cnt_t = t.off[tile + 1] - b0;
     const int64_t nch = t.chunk[tile + 1] - t.chunk[tile], k = s_part;
     p0 = (int)(b0 + cnt_t * k / nch);
-    p1 = (int)(b0 + cnt_t * (k + 1) / nch);
+    cnt = (int)(b0 + cnt_t * (k + 1) / nch) - p0;
   }
-  // particles are cell-sorted; visiting them with a stride of two spreads the particles of one
-  // cell over different warp instructions, so their deposits do not hit the same shared address
-  // in the same instruction
-  const int cnt = p1 - p0, half = (cnt + 1) >> 1;
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const int p = p0 + (j < half ? 2 * j : 2 * (j - half) + 1);
+  // visit every s-th particle (s ~ particles per cell) so that a warp's lanes hold distinct cells
+  const int s = max(1, min(8, (cnt + (t.cpt >> 1)) / t.cpt));
+  const int q = (cnt + s - 1) / s;
+  unsigned nout = 0;
+  for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
+    const int pr = interleaved(j, q, s);
+    if (pr >= cnt) continue;
+    const int p = p0 + pr;
     const int c = a.cell[p];
     const int ix = (c >> (a.shz + a.shy)) & a.mask[0], iy = (c >> a.shz) & a.mask[1], iz = c & a.mask[2];
     const float fx = a.fx[p], fy = a.fy[p], fz = a.fz[p];
@@ -316,24 +327,19 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
     shape32<P>(iz, fz, lz, Sz);
     float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int gx = lx - go0, gy = ly - go1, gz = lz - go2;
-    const bool gin = gx >= 0 && gy >= 0 && gz >= 0 && gx + NS <= G0 && gy + NS <= G1 && gz + NS <= G2;
+    const bool gin = gx >= 0 && gy >= 0 && gz >= 0 && gx + NS <= t.G[0] && gy + NS <= G1 && gz + NS <= G2;
     if (gin) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
 #pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          const float sxy = Sx[i] * Sy[j];
-          const float2* row = fld + 3 * (((gx + i) * G1 + (gy + j)) * G2 + gz);
+        for (int jj = 0; jj < NS; ++jj) {
+          const float sxy = Sx[i] * Sy[jj];
+          const float* row = fld + (gx + i) * gplane + (gy + jj) * G2 + gz;
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
-            const float s = sxy * Sz[k];
-            const float2 v0 = row[3 * k], v1 = row[3 * k + 1], v2 = row[3 * k + 2];
-            f[0] += s * v0.x;
-            f[1] += s * v0.y;
-            f[2] += s * v1.x;
-            f[3] += s * v1.y;
-            f[4] += s * v2.x;
-            f[5] += s * v2.y;
+            const float w = sxy * Sz[k];
+#pragma unroll
+            for (int qq = 0; qq < 6; ++qq) f[qq] += w * row[qq * gcomp + k];
           }
         }
       }
@@ -342,15 +348,15 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
       for (int i = 0; i < NS; ++i) {
         const int ox = ((lx + i) & a.mask[0]) * (int)a.Ny;
 #pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          const int oy = (ox + ((ly + j) & a.mask[1])) * (int)a.Nz;
-          const float sxy = Sx[i] * Sy[j];
+        for (int jj = 0; jj < NS; ++jj) {
+          const int oy = (ox + ((ly + jj) & a.mask[1])) * (int)a.Nz;
+          const float sxy = Sx[i] * Sy[jj];
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
             const int o = oy + ((lz + k) & a.mask[2]);
-            const float s = sxy * Sz[k];
+            const float w = sxy * Sz[k];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) f[q] += s * __ldg(a.F[q] + o);
+            for (int qq = 0; qq < 6; ++qq) f[qq] += w * __ldg(a.F[qq] + o);
           }
         }
       }
@@ -384,22 +390,25 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
     a.uz[p] = uz;
     const bool jin = deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
     const bool rin = deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
-    const unsigned act = __activemask();
-    const unsigned outb = __ballot_sync(act, !(gin && jin && rin));
-    if (outb && (threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(t.outside, (unsigned long long)__popc(outb));
+    nout += (gin && jin && rin) ? 0u : 1u;
   }
+  nout = __reduce_add_sync(0xffffffffu, nout);
+  if (nout && (threadIdx.x & 31) == 0) atomicAdd(t.outside, (unsigned long long)nout);
   __syncthreads();
   // flush the window: node (i, j, k) of the window is global node org + (i, j, k), wrapped
   float* dst[4] = {a.J[0], a.J[1], a.J[2], a.rho};
+  const int W1 = t.W[1], W2 = t.W[2];
+  const int vol = t.W[0] * W1 * W2;
   for (int e = threadIdx.x; e < vol; e += blockDim.x) {
-    const int k = e % t.W[2], r = e / t.W[2];
-    const int j = r % t.W[1], i = r / t.W[1];
+    const int k = e % W2, r = e / W2;
+    const int j = r % W1, i = r / W1;
     const int o = (((win.org[0] + i) & a.mask[0]) * (int)a.Ny + ((win.org[1] + j) & a.mask[1])) * (int)a.Nz +
                   ((win.org[2] + k) & a.mask[2]);
+    const int d = i * t.wplane + j * W2 + k;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float v = smem[q * vol + e];
-      if (v != 0.0f) atomicAdd(dst[q] + o, v);
+    for (int qq = 0; qq < 4; ++qq) {
+      const float v = smem[qq * t.wcomp + d];
+      if (v != 0.0f) atomicAdd(dst[qq] + o, v);
     }
   }
 }
@@ -449,23 +458,43 @@ pic_status launch_push32(pic_ctx* ctx, const Push32Args& a) {
   return PIC_OK;
 }
 
+// elements scanned per block by the multi-block exclusive scan of the binning
+constexpr int kScanBlock = 4096;
+
+// start of the chunk -> tile map inside a chunk list
+size_t chunk_map_offset(const pic_ctx* ctx) {
+  return (size_t)ctx->n_tiles + 1 + (size_t)((ctx->n_tiles + kScanBlock - 1) / kScanBlock) + 1;
+}
+
+// smallest stride >= v that is 8 (mod 32) words
+int pad_plane(int v) { return v + (((8 - v) % 32) + 32) % 32; }
+
+// tile geometry and shared-memory strides of the tiled push; returns the dynamic shared bytes
+size_t tile_layout(const pic_ctx* ctx, TileArgs& t) {
+  t.cpt = 1;
+  for (int d = 0; d < 3; ++d) {
+    t.T[d] = ctx->tile[d];
+    t.nt[d] = (int)(ctx->N[d] / ctx->tile[d]);
+    t.W[d] = ctx->tile[d] + 5;
+    t.G[d] = ctx->tile[d] + 3;
+    t.cpt *= ctx->tile[d];
+  }
+  t.wplane = pad_plane(t.W[1] * t.W[2]);
+  t.wcomp = t.W[0] * t.wplane;
+  t.gplane = pad_plane(t.G[1] * t.G[2]);
+  t.gcomp = t.G[0] * t.gplane;
+  return (4 * (size_t)t.wcomp + 6 * (size_t)t.gcomp) * sizeof(float);
+}
+
 pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t* off, const uint32_t* chunk) {
   if (a.n == 0) return PIC_OK;
   TileArgs t;
   t.off = off;
   t.chunk = chunk;
+  t.chunk_tile = chunk + chunk_map_offset(ctx);
   t.n_tiles = ctx->n_tiles;
   t.outside = ctx->bin_outside;
-  int vol = 1;
-  for (int d = 0; d < 3; ++d) {
-    t.T[d] = ctx->tile[d];
-    t.nt[d] = (int)(ctx->N[d] / ctx->tile[d]);
-    t.W[d] = ctx->tile[d] + 5;
-    vol *= t.W[d];
-  }
-  size_t gvol = 1;
-  for (int d = 0; d < 3; ++d) gvol *= (size_t)(ctx->tile[d] + 3);
-  const size_t smem = 4 * (size_t)vol * sizeof(float) + 6 * gvol * sizeof(float);
+  const size_t smem = tile_layout(ctx, t);
   // sum over tiles of ceil(count / kTileChunk) < n_tiles + n / kTileChunk: surplus CTAs return at once
   const unsigned nb = (unsigned)(ctx->n_tiles + (a.n + kTileChunk - 1) / kTileChunk);
   if (smem > 48 * 1024) {
@@ -484,7 +513,7 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
 
 // ---------------------------------------------------------------------------
 // binning of the FP32 SoA: counting sort by cell in tile-major order
-// key = tile * cells_per_tile + local cell (z fastest), so particles end up grouped by
+// key = tile * cells_per_tile + local cell (z fastest, then x, then y), so particles end up grouped by
 // tile and, inside a tile, ordered by cell (integer only: from the cell index)
 // ---------------------------------------------------------------------------
 // Binning runs only when *gate is non-zero (the device decides, see bin_decide_kernel), so it can
@@ -512,7 +541,7 @@ struct Key32Args {
   int tshift[3];
   int tmask[3];
   int64_t nty, ntz;
-  int lshift_y, lshift_z;  // log2 of the tile edge in y, z (local cell index)
+  int lshift_x, lshift_z;  // log2 of the tile edge in x, z (local cell index: z fastest, then x, then y)
   int cpt_shift;           // log2 cells per tile
   int32_t* key;
   uint32_t* counts;
@@ -525,7 +554,7 @@ __global__ void key32_kernel(Key32Args a) {
   const int c = a.cell[p];
   const int cx = (c >> (a.shz + a.shy)) & a.mask[0], cy = (c >> a.shz) & a.mask[1], cz = c & a.mask[2];
   const int t = (int)(((cx >> a.tshift[0]) * a.nty + (cy >> a.tshift[1])) * a.ntz + (cz >> a.tshift[2]));
-  const int local = ((((cx & a.tmask[0]) << a.lshift_y) | (cy & a.tmask[1])) << a.lshift_z) | (cz & a.tmask[2]);
+  const int local = ((((cy & a.tmask[1]) << a.lshift_x) | (cx & a.tmask[0])) << a.lshift_z) | (cz & a.tmask[2]);
   const int k = (t << a.cpt_shift) | local;
   a.key[p] = k;
   const unsigned active = __activemask();
@@ -536,7 +565,6 @@ __global__ void key32_kernel(Key32Args a) {
 
 // exclusive scan, phase 1: each block scans 4096 counts in place (to offsets within the block)
 // and writes its total to bsum[block]
-constexpr int kScanBlock = 4096;
 __global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n, uint32_t* bsum, const int* gate) {
   if (gated_off(gate)) return;
   __shared__ uint32_t part[1024];
@@ -604,6 +632,13 @@ __global__ void scan_add_kernel(uint32_t* v, int64_t n, const uint32_t* bsum, in
     if ((i & ((int64_t(1) << cpt_shift) - 1)) == 0) tile_off[i >> cpt_shift] = (int64_t)o;
   }
   if (i == 0) tile_off[n_tiles] = (int64_t)*total;
+}
+
+// map[k] = tile of chunk k, for the chunks [start[t], start[t + 1]) of every tile t
+__global__ void chunk_map_kernel(const uint32_t* start, int64_t n_tiles, uint32_t* map, const int* gate) {
+  if (gated_off(gate)) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tiles; t += (int64_t)gridDim.x * blockDim.x)
+    for (uint32_t k = start[t]; k < start[t + 1]; ++k) map[k] = (uint32_t)t;
 }
 
 // chunks per tile: nch[t] = ceil(count_t / kTileChunk), scanned in place afterwards
@@ -694,17 +729,13 @@ pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float*
 }
 
 bool tiled_push_fits(const pic_ctx* ctx) {
-  size_t vol = 1, gvol = 1;
-  for (int d = 0; d < 3; ++d) {
-    vol *= (size_t)(ctx->tile[d] + 5);
-    gvol *= (size_t)(ctx->tile[d] + 3);
-  }
-  return (4 * vol + 6 * gvol) * sizeof(float) <= 160 * 1024 && ctx->ncell < (int64_t(1) << 31);
+  TileArgs t;
+  return tile_layout(ctx, t) <= 160 * 1024 && ctx->ncell < (int64_t(1) << 31);
 }
 
-size_t tile_chunk_words(const pic_ctx* ctx) {
-  // chunk starts [n_tiles + 1], scan block sums, scan total
-  return (size_t)ctx->n_tiles + 1 + (size_t)((ctx->n_tiles + kScanBlock - 1) / kScanBlock) + 1;
+size_t tile_chunk_words(const pic_ctx* ctx, int64_t n) {
+  // chunk starts [n_tiles + 1], scan block sums, scan total, tile of each chunk
+  return chunk_map_offset(ctx) + (size_t)ctx->n_tiles + (size_t)(n / kTileChunk) + 1;
 }
 
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
@@ -760,7 +791,7 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   }
   b.nty = ctx->N[1] / ctx->tile[1];
   b.ntz = ctx->N[2] / ctx->tile[2];
-  b.lshift_y = ilog2(ctx->tile[1]);
+  b.lshift_x = ilog2(ctx->tile[0]);
   b.lshift_z = ilog2(ctx->tile[2]);
   b.cpt_shift = ilog2(ctx->tile[0]) + ilog2(ctx->tile[1]) + ilog2(ctx->tile[2]);
   b.key = ctx->bin_tid;
@@ -791,6 +822,8 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
     scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(cbsum, nblk_t, ctotal, gate);
     PIC_LAUNCH_CHECK(ctx);
     chunk_add_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(chunks_out, nt, cbsum, ctotal, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    chunk_map_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(chunks_out, nt, chunks_out + chunk_map_offset(ctx), gate);
     PIC_LAUNCH_CHECK(ctx);
   }
   if (n == 0) return PIC_OK;

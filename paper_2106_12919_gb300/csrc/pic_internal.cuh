@@ -127,7 +127,8 @@ struct pic_ctx {
   // FP32 form: per-species tile ranges of the last binning inside pic_step32
   int64_t* sp_off[PIC_MAX_BINNED_SPECIES];
   int64_t sp_off_n[PIC_MAX_BINNED_SPECIES];   // particle count they were built for, -1 = invalid
-  uint32_t* sp_chunk[PIC_MAX_BINNED_SPECIES];  // per-species chunk starts of the tiled push (see below)
+  uint32_t* sp_chunk[PIC_MAX_BINNED_SPECIES];  // per-species chunk lists of the tiled push (see below)
+  int64_t sp_chunk_n[PIC_MAX_BINNED_SPECIES];  // particle count the chunk list was sized for
   Timers timers;
   char err[256];
 };
@@ -215,12 +216,12 @@ pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float*
                             const pic_species32* sp, float* const J[3], float* rho);
 pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float* rho);
 // Tiled push: one CTA per chunk of at most kTileChunk particles of one tile, over the ranges
-// offsets[n_tiles + 1] of the last binning; chunks[n_tiles + 1] holds the exclusive prefix sum
-// of the tiles' chunk counts.  Shared-memory deposit window per chunk.  Correct for any order
+// offsets[n_tiles + 1] of the last binning; chunks holds the exclusive prefix sum of the
+// tiles' chunk counts [n_tiles + 1], its scan scratch, and the tile of every chunk.  Shared-memory deposit window per chunk.  Correct for any order
 // (out-of-window deposits go global).
 constexpr int kTileChunk = 2048;
 bool tiled_push_fits(const pic_ctx* ctx);  // deposit window of the tile fits in shared memory
-size_t tile_chunk_words(const pic_ctx* ctx);  // size of a chunks array incl. its scan scratch
+size_t tile_chunk_words(const pic_ctx* ctx, int64_t n);  // chunk list size for n particles (words)
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                                   const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets,
                                   const uint32_t* chunks);

@@ -103,18 +103,21 @@ __device__ __forceinline__ void deposit_node_block(const Push32Args& a, int ix, 
 }
 
 // Shared-memory deposit window of one tile: nodes [org, org + W) per axis
-// (unwrapped coordinates), four FP32 components (J^x, J^y, J^z, rho), each
-// [W0][W1][W2] with row stride W2 and plane stride `plane` (padded, see TileArgs).
+// (unwrapped coordinates), four fixed-point int32 components (J^x, J^y, J^z, rho;
+// value = sum / scale), each [W0][W1][W2] with row stride W2 and plane stride
+// `plane` (padded, see TileArgs).
 struct Window {
-  float* acc;
+  int* acc;
   int org[3];
   int W[3];
   int plane, comp;
+  float sj[3], sr;  // fixed-point scales (powers of two) of the J^x, J^y, J^z and rho sums
 };
 
 // Deposit one particle's (P+1)^3 block: inside the window with shared-memory
-// atomics, outside it (a particle that left its tile since the last binning)
-// with global atomics.  j: (v0, v1, v2) into J, else r into rho.
+// integer atomics of the contributions rounded to the window's fixed-point scale,
+// outside it (a particle that left its tile since the last binning) with global
+// FP32 atomics.  j: (v0, v1, v2) into J, else r into rho.
 template <int P>
 __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window& win, int ix, int iy, int iz,
                                                float fx, float fy, float fz, float v0, float v1, float v2, float r,
@@ -134,21 +137,22 @@ __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window
     return false;
   }
   const int comp = win.comp;
+  const float w0 = v0 * win.sj[0], w1 = v1 * win.sj[1], w2 = v2 * win.sj[2], wr = r * win.sr;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
 #pragma unroll
     for (int jj = 0; jj < NS; ++jj) {
       const float sxy = Sx[i] * Sy[jj];
-      float* row = win.acc + (wx + i) * win.plane + (wy + jj) * win.W[2] + wz;
+      int* row = win.acc + (wx + i) * win.plane + (wy + jj) * win.W[2] + wz;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         const float s = sxy * Sz[k];
         if (j) {
-          atomicAdd(row + k, s * v0);
-          atomicAdd(row + comp + k, s * v1);
-          atomicAdd(row + 2 * comp + k, s * v2);
+          atomicAdd(row + k, __float2int_rn(s * w0));
+          atomicAdd(row + comp + k, __float2int_rn(s * w1));
+          atomicAdd(row + 2 * comp + k, __float2int_rn(s * w2));
         } else {
-          atomicAdd(row + 3 * comp + k, s * r);
+          atomicAdd(row + 3 * comp + k, __float2int_rn(s * wr));
         }
       }
     }
@@ -263,6 +267,7 @@ template <int P>
 __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileArgs t) {
   extern __shared__ float smem[];
   __shared__ int s_tile, s_part;
+  __shared__ float s_bnd[4][8];
   if (threadIdx.x == 0) {
     // chunk blockIdx.x: its tile from the chunk map, its index within the tile from the chunk starts
     const uint32_t b = blockIdx.x;
@@ -285,10 +290,17 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
   for (int d = 0; d < 3; ++d) win.W[d] = t.W[d];
   win.plane = t.wplane;
   win.comp = t.wcomp;
-  win.acc = smem;
+  win.acc = reinterpret_cast<int*>(smem);
   const int G1 = t.G[1], G2 = t.G[2], gplane = t.gplane, gcomp = t.gcomp;
   float* fld = smem + 4 * t.wcomp;  // [6][G0][G1][G2], plane stride gplane
   const int go0 = tx * t.T[0] - 1, go1 = ty * t.T[1] - 1, go2 = tz * t.T[2] - 1;
+  int p0, cnt;
+  {
+    const int64_t b0 = t.off[tile], cnt_t = t.off[tile + 1] - b0;
+    const int64_t nch = t.chunk[tile + 1] - t.chunk[tile], k = s_part;
+    p0 = (int)(b0 + cnt_t * k / nch);
+    cnt = (int)(b0 + cnt_t * (k + 1) / nch) - p0;
+  }
   for (int e = threadIdx.x; e < 4 * t.wcomp; e += blockDim.x) smem[e] = 0.0f;
   const int gvol = t.G[0] * G1 * G2;
   for (int e = threadIdx.x; e < gvol; e += blockDim.x) {
@@ -301,17 +313,13 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
   }
   __syncthreads();
   constexpr int NS = P + 1;
-  int p0, cnt;
-  {
-    const int64_t b0 = t.off[tile], cnt_t = t.off[tile + 1] - b0;
-    const int64_t nch = t.chunk[tile + 1] - t.chunk[tile], k = s_part;
-    p0 = (int)(b0 + cnt_t * k / nch);
-    cnt = (int)(b0 + cnt_t * (k + 1) / nch) - p0;
-  }
   // visit every s-th particle (s ~ particles per cell) so that a warp's lanes hold distinct cells
   const int s = max(1, min(8, (cnt + (t.cpt >> 1)) / t.cpt));
   const int q = (cnt + s - 1) / s;
   unsigned nout = 0;
+  // Phase 1: gather, Boris push and move of every particle of the chunk; the new state goes to
+  // memory.  Each thread sums |q w v_c| (c = x, y, z) and |q w| over its particles.
+  float bnd[4] = {0.f, 0.f, 0.f, 0.f};
   for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
     const int pr = interleaved(j, q, s);
     if (pr >= cnt) continue;
@@ -319,7 +327,6 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
     const int c = a.cell[p];
     const int ix = (c >> (a.shz + a.shy)) & a.mask[0], iy = (c >> a.shz) & a.mask[1], iz = c & a.mask[2];
     const float fx = a.fx[p], fy = a.fy[p], fz = a.fz[p];
-    const float qw = a.w[p] * a.qw_scale;
     int lx, ly, lz;
     float Sx[NS], Sy[NS], Sz[NS];
     shape32<P>(ix, fx, lx, Sx);
@@ -360,6 +367,7 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
           }
         }
       }
+      ++nout;
     }
     const float kq = a.qm_half_dt;
     const float umx = a.ux[p] + kq * f[0], umy = a.uy[p] + kq * f[1], umz = a.uz[p] + kq * f[2];
@@ -376,9 +384,7 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
     const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
     const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
     const float dX = a.dtdx[0] * (vx - a.vg[0]), dY = a.dtdx[1] * (vy - a.vg[1]), dZ = a.dtdx[2] * (vz - a.vg[2]);
-    float mfx, mfy, mfz, nfx, nfy, nfz;
-    const int mx = ix + move_offset(fx, 0.5f * dX, mfx), my = iy + move_offset(fy, 0.5f * dY, mfy),
-              mz = iz + move_offset(fz, 0.5f * dZ, mfz);
+    float nfx, nfy, nfz;
     const int nx = ix + move_offset(fx, dX, nfx), ny = iy + move_offset(fy, dY, nfy),
               nz = iz + move_offset(fz, dZ, nfz);
     a.cell[p] = (((nx & a.mask[0]) * (int)a.Ny + (ny & a.mask[1])) * (int)a.Nz) + (nz & a.mask[2]);
@@ -388,15 +394,73 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
     a.ux[p] = ux;
     a.uy[p] = uy;
     a.uz[p] = uz;
+    const float qw = fabsf(a.w[p] * a.qw_scale);
+    bnd[0] += qw * fabsf(vx);
+    bnd[1] += qw * fabsf(vy);
+    bnd[2] += qw * fabsf(vz);
+    bnd[3] += qw;
+  }
+  // Fixed-point scales.  A node sum of component c is at most S_max^3 sum_p |q w v_c| (J) or
+  // S_max^3 sum_p |q w| (rho), S_max the largest 1D shape weight; each scale is the power of
+  // two that puts this bound below 2^30, so the int32 sums (plus at most 1/2 per rounded
+  // contribution) cannot overflow, and every contribution is rounded to 2^-30 of the chunk's
+  // own bound: the window sums are exact integers, independent of the atomic order.
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bnd[c] += __shfl_xor_sync(0xffffffffu, bnd[c], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s_bnd[c][threadIdx.x >> 5] = bnd[c];
+  }
+  __syncthreads();
+  float scale[4];
+  {
+    const float smax3 = P == 1 ? 1.0f : (P == 2 ? 0.421875f : 0.2962963f);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float b = 0.0f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bnd[c][w];
+      b *= smax3 * 1.001f;  // margin for the rounding of the sums and of S_max^3
+      // b < 2^(ilogb(b) + 1), so b * 2^(29 - ilogb(b)) < 2^30
+      scale[c] = b > 0.0f ? ldexpf(1.0f, min(126, max(-126, 29 - ilogbf(b)))) : 1.0f;
+    }
+  }
+  win.sj[0] = scale[0];
+  win.sj[1] = scale[1];
+  win.sj[2] = scale[2];
+  win.sr = scale[3];
+  // Phase 2: deposit J^{n+1/2} at the midpoint x^{n+1} - (dt/2)(v - v_gal) and rho^{n+1} at
+  // x^{n+1}, from the state written in phase 1 (same thread, same particles).
+  for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
+    const int pr = interleaved(j, q, s);
+    if (pr >= cnt) continue;
+    const int p = p0 + pr;
+    const int c = a.cell[p];
+    const int nx = (c >> (a.shz + a.shy)) & a.mask[0], ny = (c >> a.shz) & a.mask[1], nz = c & a.mask[2];
+    const float nfx = a.fx[p], nfy = a.fy[p], nfz = a.fz[p];
+    const float ux = a.ux[p], uy = a.uy[p], uz = a.uz[p];
+    const float qw = a.w[p] * a.qw_scale;
+    const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
+    const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
+    const float hX = -0.5f * a.dtdx[0] * (vx - a.vg[0]), hY = -0.5f * a.dtdx[1] * (vy - a.vg[1]),
+                hZ = -0.5f * a.dtdx[2] * (vz - a.vg[2]);
+    float mfx, mfy, mfz;
+    const int mx = nx + move_offset(nfx, hX, mfx), my = ny + move_offset(nfy, hY, mfy),
+              mz = nz + move_offset(nfz, hZ, mfz);
     const bool jin = deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
     const bool rin = deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
-    nout += (gin && jin && rin) ? 0u : 1u;
+    nout += (jin && rin) ? 0u : 1u;
   }
   nout = __reduce_add_sync(0xffffffffu, nout);
   if (nout && (threadIdx.x & 31) == 0) atomicAdd(t.outside, (unsigned long long)nout);
   __syncthreads();
   // flush the window: node (i, j, k) of the window is global node org + (i, j, k), wrapped
   float* dst[4] = {a.J[0], a.J[1], a.J[2], a.rho};
+  float inv[4];  // exact: the scales are powers of two
+#pragma unroll
+  for (int c = 0; c < 4; ++c) inv[c] = 1.0f / scale[c];
   const int W1 = t.W[1], W2 = t.W[2];
   const int vol = t.W[0] * W1 * W2;
   for (int e = threadIdx.x; e < vol; e += blockDim.x) {
@@ -407,8 +471,8 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
     const int d = i * t.wplane + j * W2 + k;
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
-      const float v = smem[qq * t.wcomp + d];
-      if (v != 0.0f) atomicAdd(dst[qq] + o, v);
+      const int iv = win.acc[qq * t.wcomp + d];
+      if (iv != 0) atomicAdd(dst[qq] + o, (float)iv * inv[qq]);
     }
   }
 }

@@ -210,6 +210,7 @@ def main():
         "clocks": head["clocks"],
         "e2e": head["e2e"],
         "roofline": head["roofline"],
+        "fft_reference": head["fft_reference"],
     }
     if "fp64" in res and forms[0] != "fp64":
         r64 = res["fp64"]
@@ -226,6 +227,33 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def cufft_reference(shape, dtype, libpic_ms):
+    """cuFFT (through torch.fft) on the step's transform load, timed as a reference only:
+    4 forward R2C (J, rho) and 6 inverse C2R (nodal E, B) 3D transforms of the grid."""
+    import torch
+    x = torch.randn((4,) + tuple(shape), dtype=dtype, device="cuda")
+    y = torch.randn((6,) + tuple(shape), dtype=dtype, device="cuda")
+    dims = (1, 2, 3)
+
+    Ys = torch.fft.rfftn(y, dim=dims)
+    for _ in range(3):
+        torch.fft.rfftn(x, dim=dims)
+        torch.fft.irfftn(Ys, s=tuple(shape), dim=dims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        torch.fft.rfftn(x, dim=dims)
+        torch.fft.irfftn(Ys, s=tuple(shape), dim=dims)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del x, y, Ys
+    torch.cuda.empty_cache()
+    return {"cufft_ms_per_step": ms, "libpic_fft_ms_per_step": libpic_ms,
+            "note": "cuFFT via torch.fft: 4 R2C + 6 C2R 3D transforms of the grid per step, reference only"}
 
 
 def run_form(form, w, args, world, rank, local):
@@ -340,7 +368,9 @@ def run_form(form, w, args, world, rank, local):
     esz = 4 if fp32 else 8
     resident = (10 * ncell * esz + sum(sum(a.numel() * a.element_size() for a in s.arrays()) for s in sp)
                 + 40 * ncell * esz) / 1e9
+    fft_ref = cufft_reference(shape, tdt, stage["fft"][0] / args.steps)
     out = {"value": value, "ms": ms, "npart": npart, "clocks": clocks, "e2e": e2e, "roofline": roofline,
+           "fft_reference": fft_ref,
            "stage_ms": {k: v[0] / args.steps for k, v in stage.items() if k != "all"},
            "launches": stage["all"][1], "bytes_resident": resident}
     ctx.close()

@@ -162,10 +162,22 @@ __global__ void __launch_bounds__(kMaxThreads) fft_z_r2c_kernel(CRP6<T> in, CP6<
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
   const C* src = reinterpret_cast<const C*>(in.p[comp]);
-  for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-    const int l = t / M, e = t - l * M;
-    const int64_t line = line0 + l;
-    sm[lay.idx(e, l)] = line < nlines ? src[line * M + e] : czero<C>();
+  {
+    // L * M == 8 * blockDim.x: 8 elements per thread, loads issued back to back
+    C v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int t = threadIdx.x + q * blockDim.x;
+      const int l = t / M;
+      const int64_t line = line0 + l;
+      v[q] = line < nlines ? src[line * M + (t - l * M)] : czero<C>();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int t = threadIdx.x + q * blockDim.x;
+      const int l = t / M;
+      sm[lay.idx(t - l * M, l)] = v[q];
+    }
   }
   __syncthreads();
   fft_tile<false>(sm, lay, M, tw, 2);
@@ -249,10 +261,16 @@ __global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CP6<C> data, i
   const int col0 = blockIdx.x * W;
   C* base = data.p[comp] + (int64_t)blockIdx.y * os + col0;
   const int wv = min(W, ncols - col0);
-  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
+  // N * W == 8 * blockDim.x: every thread moves 8 elements; the 8 loads are issued back to back
+  C v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
     const int e = t / W, w = t - e * W;
-    sm[t] = w < wv ? base[e * es + w] : czero<C>();
+    v[q] = w < wv ? base[e * es + w] : czero<C>();
   }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) sm[threadIdx.x + q * blockDim.x] = v[q];
   __syncthreads();
   fft_tile<INV>(sm, lay, N, tw, 1);
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {

@@ -22,21 +22,25 @@ namespace {
 constexpr int kZTile = 4096;    // complex elements per z-pass CTA (L lines * Nz/2)
 constexpr int kMaxThreads = 1024;
 
+// All sizes are powers of two: index arithmetic uses shifts and masks (lg* = log2).
+__device__ __forceinline__ int lg2(int v) { return __ffs(v) - 1; }
+
 struct LayLine {  // z pass: element e of line l at l * LP + e + e / 8
   int LP;
   __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + (e >> 3); }
-  __device__ __forceinline__ void map(int b, int nb, int& l, int& j) const {
-    l = b / nb;
-    j = b - l * nb;
+  // butterfly b of nb = 2^lgnb per line -> line l, index j
+  __device__ __forceinline__ void map(int b, int lgnb, int& l, int& j) const {
+    l = b >> lgnb;
+    j = b & ((1 << lgnb) - 1);
   }
 };
 
-struct LayCol {  // y / x pass: element e of column w at e * W + w
-  int W;
-  __device__ __forceinline__ int idx(int e, int w) const { return e * W + w; }
-  __device__ __forceinline__ void map(int b, int nb, int& l, int& j) const {
-    j = b / W;
-    l = b - j * W;
+struct LayCol {  // y / x pass: element e of column w at e * W + w, W = 2^lgW
+  int lgW;
+  __device__ __forceinline__ int idx(int e, int w) const { return (e << lgW) + w; }
+  __device__ __forceinline__ void map(int b, int lgnb, int& l, int& j) const {
+    j = b >> lgW;
+    l = b & ((1 << lgW) - 1);
   }
 };
 
@@ -98,18 +102,20 @@ __device__ __forceinline__ void dft(C* v) {
 // One Stockham pass of radix R on all lines of the tile, in place.  The CTA has
 // exactly L * N / 8 threads; each thread handles 8 / R butterflies.
 template <int R, bool INV, class C, class LAY>
-__device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int N, int Ns, const C* __restrict__ tw,
+__device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int lgN, int lgNs, const C* __restrict__ tw,
                                               int twstride) {
   constexpr int PER = 8 / R;
+  constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
   const int T = blockDim.x;
-  const int nb = N / R;
+  const int lgnb = lgN - LGR;
+  const int nb = 1 << lgnb, Ns = 1 << lgNs;
   C v[PER][R];
   int ol[PER], oj[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     int b = threadIdx.x + q * T;
     int l, j;
-    lay.map(b, nb, l, j);
+    lay.map(b, lgnb, l, j);
     ol[q] = l;
     oj[q] = j;
 #pragma unroll
@@ -121,7 +127,7 @@ __device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int N, int N
     const int j = oj[q], l = ol[q];
     const int k = j & (Ns - 1);
     if (Ns > 1) {
-      const int step = (N / (Ns * R)) * k;
+      const int step = k << (lgN - lgNs - LGR);  // (N / (Ns R)) k
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         C w = __ldg(&tw[step * r * twstride]);
@@ -139,14 +145,15 @@ __device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int N, int N
 
 template <bool INV, class C, class LAY>
 __device__ void fft_tile(C* s, const LAY& lay, int N, const C* __restrict__ tw, int twstride) {
-  int Ns = 1, rem = N;
-  while (rem >= 8) {
-    stockham_pass<8, INV>(s, lay, N, Ns, tw, twstride);
-    Ns *= 8;
-    rem /= 8;
+  const int lgN = lg2(N);
+  int lgNs = 0, rem = lgN;
+  while (rem >= 3) {
+    stockham_pass<8, INV>(s, lay, lgN, lgNs, tw, twstride);
+    lgNs += 3;
+    rem -= 3;
   }
-  if (rem == 4) stockham_pass<4, INV>(s, lay, N, Ns, tw, twstride);
-  else if (rem == 2) stockham_pass<2, INV>(s, lay, N, Ns, tw, twstride);
+  if (rem == 2) stockham_pass<4, INV>(s, lay, lgN, lgNs, tw, twstride);
+  else if (rem == 1) stockham_pass<2, INV>(s, lay, lgN, lgNs, tw, twstride);
 }
 
 // z-axis real-to-complex: L lines of Nz reals -> Nz/2+1 complex per line.
@@ -165,18 +172,18 @@ __global__ void __launch_bounds__(kMaxThreads) fft_z_r2c_kernel(CRP6<T> in, CP6<
   {
     // L * M == 8 * blockDim.x: 8 elements per thread, loads issued back to back
     C v[8];
+    const int lgM = lg2(M);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int t = threadIdx.x + q * blockDim.x;
-      const int l = t / M;
+      const int l = t >> lgM;
       const int64_t line = line0 + l;
-      v[q] = line < nlines ? src[line * M + (t - l * M)] : czero<C>();
+      v[q] = line < nlines ? src[line * M + (t & (M - 1))] : czero<C>();
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int t = threadIdx.x + q * blockDim.x;
-      const int l = t / M;
-      sm[lay.idx(t - l * M, l)] = v[q];
+      sm[lay.idx(t & (M - 1), t >> lgM)] = v[q];
     }
   }
   __syncthreads();
@@ -185,8 +192,13 @@ __global__ void __launch_bounds__(kMaxThreads) fft_z_r2c_kernel(CRP6<T> in, CP6<
   C* dst = out.p[comp];
   const int nzh = M + 1, P = M / 2 + 1;
   const T h = (T)0.5;
-  for (int t = threadIdx.x; t < L * P; t += blockDim.x) {
-    const int l = t / P, k = t - l * P;
+  // k = 0 .. M/2 - 1 for every line (t < L M / 2), then k = M/2 (t >= L M / 2)
+  const int lgH = lg2(M) - 1;
+  (void)P;
+  for (int t = threadIdx.x; t < (L << lgH) + L; t += blockDim.x) {
+    const bool mid = t >= (L << lgH);
+    const int l = mid ? t - (L << lgH) : t >> lgH;
+    const int k = mid ? (M >> 1) : t & ((M >> 1) - 1);
     const int64_t line = line0 + l;
     if (line >= nlines) continue;
     const C Zk = sm[lay.idx(k, l)];
@@ -218,14 +230,31 @@ __global__ void __launch_bounds__(kMaxThreads) fft_z_c2r_kernel(CP6<typename Cpl
   const C* srcb = in.p[comp];
   const int nzh = M + 1, P = M / 2 + 1;
   // Z_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
-  for (int t = threadIdx.x; t < L * P; t += blockDim.x) {
-    const int l = t / P, k = t - l * P;
+  // k = 0 .. M/2 - 1 for every line (t < L M / 2), then k = M/2 (t >= L M / 2)
+  constexpr int kBatch = 5;  // L * P <= 5 * blockDim.x for every M >= 8 (L * M = 8 * blockDim.x)
+  const int lgH = lg2(M) - 1;
+  C xk[kBatch], xm[kBatch];
+#pragma unroll
+  for (int q = 0; q < kBatch; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    const bool mid = t >= (L << lgH);
+    const int l = mid ? t - (L << lgH) : t >> lgH;
+    const int k = mid ? (M >> 1) : t & ((M >> 1) - 1);
     const int64_t line = line0 + l;
-    C Xk = czero<C>(), Xm = czero<C>();
-    if (line < nlines) {
-      Xk = srcb[line * nzh + k];
-      Xm = srcb[line * nzh + (M - k)];
+    xk[q] = xm[q] = czero<C>();
+    if (t < L * P && line < nlines) {
+      xk[q] = srcb[line * nzh + k];
+      xm[q] = srcb[line * nzh + (M - k)];
     }
+  }
+#pragma unroll
+  for (int q = 0; q < kBatch; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t >= L * P) break;
+    const bool mid = t >= (L << lgH);
+    const int l = mid ? t - (L << lgH) : t >> lgH;
+    const int k = mid ? (M >> 1) : t & ((M >> 1) - 1);
+    C Xk = xk[q], Xm = xm[q];
     if (k == 0) {
       Xk.y = 0;
       Xm.y = 0;
@@ -242,8 +271,9 @@ __global__ void __launch_bounds__(kMaxThreads) fft_z_c2r_kernel(CP6<typename Cpl
   __syncthreads();
   fft_tile<true>(sm, lay, M, tw, 2);
   C* dst = reinterpret_cast<C*>(out.p[comp]);
+  const int lgM = lg2(M);
   for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-    const int l = t / M, e = t - l * M;
+    const int l = t >> lgM, e = t & (M - 1);
     const int64_t line = line0 + l;
     if (line < nlines) dst[line * M + e] = sm[lay.idx(e, l)];
   }
@@ -256,7 +286,8 @@ __global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CP6<C> data, i
                                                                  int ncols, int W, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const LayCol lay{W};
+  const int lgW = lg2(W);
+  const LayCol lay{lgW};
   const int comp = blockIdx.z;
   const int col0 = blockIdx.x * W;
   C* base = data.p[comp] + (int64_t)blockIdx.y * os + col0;
@@ -266,7 +297,7 @@ __global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CP6<C> data, i
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int t = threadIdx.x + q * blockDim.x;
-    const int e = t / W, w = t - e * W;
+    const int e = t >> lgW, w = t & (W - 1);
     v[q] = w < wv ? base[e * es + w] : czero<C>();
   }
 #pragma unroll
@@ -274,7 +305,7 @@ __global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CP6<C> data, i
   __syncthreads();
   fft_tile<INV>(sm, lay, N, tw, 1);
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
-    const int e = t / W, w = t - e * W;
+    const int e = t >> lgW, w = t & (W - 1);
     if (w < wv) base[e * es + w] = sm[t];
   }
 }

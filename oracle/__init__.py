@@ -22,7 +22,9 @@ psatd        Standard / Galilean / averaged-Galilean PSATD coefficients and
              k-space updates (Sec. 4.2-4.4).
 particles    B-spline shapes, gather, Boris push, direct deposition, tile bins.
 step         The hybrid PIC cycle of Sec. 2.
-diagnostics  Field energy (Sec. 2 (iii)) and the L2 error norm (Sec. 5.2).
+diagnostics  Field energy (Sec. 2 (iii)), the L2 error norm (Sec. 5.2), the stencil
+             extent (Eq. stencil_extent), the beam RMS (Eq. RMS_pwfa) and the numerical
+             vacuum dispersion of an update (Sec. 2 (i), App. B).
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, brute force or invariants, except the full multi-step cycle,

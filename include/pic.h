@@ -352,6 +352,48 @@ pic_status pic_field_energy32(pic_ctx* ctx, const float* const E[3], const float
 pic_status pic_total_charge32(pic_ctx* ctx, const float* rho, double* out);
 
 /*
+ * ---- Diagnostics (not on the step's hot path; FP64 arithmetic; HOST results) ----
+ *
+ * pic_stencil_extent: stencil extent of the coefficient table `coef` (names as in
+ * pic_coefficient) along axis 0, 1 or 2 (Sec. 2 (ii), Eq. stencil_extent): the
+ * modulus of the inverse DFT of the table along the axis, averaged over the Fourier
+ * indices of the two other axes (over their full range: the stored half spectrum is
+ * extended by g(-k) = conj g(k)).  out: HOST, N_axis doubles, out[j] = Gamma(j dx_axis)
+ * (periodic: j > N/2 are the offsets j - N).  Any context precision.  Synchronous.
+ */
+pic_status pic_stencil_extent(pic_ctx* ctx, const char* coef, int axis, double* out);
+
+/*
+ * pic_axis_tables: the 1D tables of axis a used by the update, HOST copies of N_a
+ * doubles each in FFT order (k_j = 2 pi m_j / (N_a dx_a), m_j the signed index with the
+ * Nyquist index at -N_a/2): ks = [k]_s and kc = [k]_c at the context's spectral order
+ * (Sec. 4.1, Eqs. k_staggered / k_centered) and zeta = zeta_F, the Fourier symbol of the
+ * centering of order centering_order[a] (App. C).  Any pointer may be NULL.  Synchronous.
+ */
+pic_status pic_axis_tables(pic_ctx* ctx, int axis, double* ks, double* kc, double* zeta);
+
+/*
+ * pic_vacuum_dispersion: numerical vacuum frequency of the context's update for waves
+ * along axis a (Sec. 2 (i), App. B): per Fourier index along the axis (the other two
+ * indices 0) the transverse block of the update, [[TC, -i c^2 TS [k]_s], [-i TS [k]_s, TC]],
+ * has eigenvalues TC +- i c TS [k]_s; omega = (larger eigenvalue phase) / dt.  Standard
+ * PSATD gives omega = c |[k]_s|; Galilean phases are shifted by Omega_c dt.  omega: HOST,
+ * N_a doubles, FFT order.  Synchronous.
+ */
+pic_status pic_vacuum_dispersion(pic_ctx* ctx, int axis, double* omega);
+
+/*
+ * pic_beam_rms / pic_beam_rms32: averaged transverse RMS size of a species (Sec. 5.3,
+ * Eq. RMS_pwfa): delta = 1/2 sqrt(sum w (x - <x>)^2 / sum w) + 1/2 sqrt(sum w (y - <y>)^2
+ * / sum w), <.> the w-weighted means, positions as stored (no periodic unwrapping; FP32
+ * form: x = (ix + fx) dx in FP64).  delta: HOST.  PIC_ERR_ARG for an empty species or a
+ * non-positive weight sum.  Synchronous.
+ */
+pic_status pic_beam_rms(pic_ctx* ctx, const pic_species* sp, double* delta);
+pic_status pic_beam_rms32(pic_ctx* ctx, const pic_species32* sp, double* delta);
+
+
+/*
  * pic_center_to_nodal_static: the same centering as pic_center_to_nodal, for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this exists for host programs that own every byte of device memory through

@@ -6,6 +6,14 @@
 #include <cstdlib>
 #include <new>
 
+int coef_index(const pic_ctx* ctx, const char* name) {
+  static const char* names[COEF_COUNT] = {"TC", "TS", "X1", "X2", "TX3", "X4",
+                                          "Psi1", "Psi2", "Y1", "Y2", "Y3", "Y4"};
+  for (int k = 0; k < ctx->ncoef; ++k)
+    if (strcmp(names[k], name) == 0) return k;
+  return -1;
+}
+
 pic_status pic_set_error(pic_ctx* ctx, pic_status st, const char* fmt, ...) {
   if (ctx) {
     va_list ap;
@@ -362,15 +370,11 @@ pic_status pic_maxwell_step(pic_ctx* ctx, double* const E[3], double* const B[3]
 pic_status pic_coefficient(pic_ctx* ctx, const char* name, double* out) {
   if (!ctx) return PIC_ERR_ARG;
   if (!name || !out) return pic_set_error(ctx, PIC_ERR_ARG, "null argument");
-  static const char* names[COEF_COUNT] = {"TC", "TS", "X1", "X2", "TX3", "X4",
-                                          "Psi1", "Psi2", "Y1", "Y2", "Y3", "Y4"};
-  for (int k = 0; k < ctx->ncoef; ++k)
-    if (strcmp(names[k], name) == 0) {
-      PIC_CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->coef + k * ctx->nmode, ctx->nmode * sizeof(double2),
-                                        cudaMemcpyDeviceToDevice, ctx->stream));
-      return PIC_OK;
-    }
-  return pic_set_error(ctx, PIC_ERR_ARG, "unknown coefficient '%s'", name);
+  const int k = coef_index(ctx, name);
+  if (k < 0) return pic_set_error(ctx, PIC_ERR_ARG, "unknown coefficient '%s'", name);
+  PIC_CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->coef + k * ctx->nmode, ctx->nmode * sizeof(double2),
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+  return PIC_OK;
 }
 
 pic_status pic_field_energy(pic_ctx* ctx, const double* const E[3], const double* const B[3],

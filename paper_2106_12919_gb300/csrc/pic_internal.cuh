@@ -205,6 +205,9 @@ pic_status psatd_adjoint_update(pic_ctx* ctx, double2* EB, double2* G);
 // EB[c] += zeta_c * src[c] (c = 0..5): transpose of the E, B -> nodal centering.
 pic_status psatd_add_zeta(pic_ctx* ctx, double2* EB, const double2* src);
 
+// index of a coefficient table by name ("TC", "TS", ..., see pic_coefficient), -1 if unknown
+int coef_index(const pic_ctx* ctx, const char* name);
+
 // particles.cu ----------------------------------------------------------------
 pic_status particles_push(pic_ctx* ctx, const double* const En[3], const double* const Bn[3],
                           const pic_species* sp, double* const J[3], double* rho);

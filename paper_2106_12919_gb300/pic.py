@@ -94,6 +94,12 @@ def _load():
         "pic_adjoint_step": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(PicSpecies), ctypes.c_int, P(_vp), P(_vp), _vp,
                                             P(PicSpeciesAdjoint)]),
         "pic_timing_read": (ctypes.c_int, [_vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_int64)]),
+        "pic_stencil_extent": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int, P(ctypes.c_double)]),
+        "pic_axis_tables": (ctypes.c_int, [_vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
+                                           P(ctypes.c_double)]),
+        "pic_vacuum_dispersion": (ctypes.c_int, [_vp, ctypes.c_int, P(ctypes.c_double)]),
+        "pic_beam_rms": (ctypes.c_int, [_vp, P(PicSpecies), P(ctypes.c_double)]),
+        "pic_beam_rms32": (ctypes.c_int, [_vp, P(PicSpecies32), P(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -109,7 +115,8 @@ EXPORTS = ("pic_ext_default", "pic_init", "pic_destroy", "pic_last_error", "pic_
            "pic_coefficient", "pic_field_energy", "pic_total_charge", "pic_timing", "pic_timing_read",
            "pic_center_to_nodal_static", "pic_step32", "pic_deposit_rho32", "pic_push_deposit32", "pic_bin32",
            "pic_fft_forward32", "pic_fft_inverse32", "pic_field_energy32", "pic_total_charge32",
-           "pic_adjoint_step")
+           "pic_adjoint_step", "pic_stencil_extent", "pic_axis_tables", "pic_vacuum_dispersion", "pic_beam_rms",
+           "pic_beam_rms32")
 
 
 def _ptr(t, n=None):
@@ -376,6 +383,37 @@ class Context:
     def total_charge32(self, rho):
         out = ctypes.c_double()
         self._check(LIB.pic_total_charge32(self.h, _ptr(rho, self.ncell), ctypes.byref(out)))
+        return out.value
+
+    # ---- diagnostics (host results) ----
+    def _axis_len(self, axis):
+        return int(self.shape[axis]) if 0 <= axis < 3 else 1  # a bad axis is rejected by the library
+
+    def stencil_extent(self, coef, axis):
+        out = (ctypes.c_double * self._axis_len(axis))()
+        self._check(LIB.pic_stencil_extent(self.h, coef.encode(), axis, out))
+        return list(out)
+
+    def axis_tables(self, axis):
+        """([k]_s, [k]_c, zeta) along the axis, FFT order."""
+        n = self._axis_len(axis)
+        ks, kc, zt = (ctypes.c_double * n)(), (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        self._check(LIB.pic_axis_tables(self.h, axis, ks, kc, zt))
+        return list(ks), list(kc), list(zt)
+
+    def vacuum_dispersion(self, axis):
+        out = (ctypes.c_double * self._axis_len(axis))()
+        self._check(LIB.pic_vacuum_dispersion(self.h, axis, out))
+        return list(out)
+
+    def beam_rms(self, species):
+        out = ctypes.c_double()
+        self._check(LIB.pic_beam_rms(self.h, _species_array([species]), ctypes.byref(out)))
+        return out.value
+
+    def beam_rms32(self, species):
+        out = ctypes.c_double()
+        self._check(LIB.pic_beam_rms32(self.h, _species_array([species]), ctypes.byref(out)))
         return out.value
 
     # ---- reverse mode ----

@@ -122,3 +122,14 @@ def positions(shape, dx, name):
     """Physical coordinates (X, Y, Z) of every element of component `name` (App. A)."""
     ax = [(np.arange(shape[a]) + 0.5 * STAG[name][a]) * dx[a] for a in range(3)]
     return np.meshgrid(*ax, indexing="ij")
+
+
+def bilinear_filter(f, passes):
+    """`passes` passes of the bilinear (1/4, 1/2, 1/4) smoothing filter along every axis
+    of a periodic array (Sec. 2: the optional smoothing of the deposited rho and J,
+    Birdsall and Langdon): f_j <- f_{j-1}/4 + f_j/2 + f_{j+1}/4, axes x, y, z in turn."""
+    g = np.asarray(f, dtype=np.float64)
+    for _ in range(int(passes)):
+        for a in range(g.ndim):
+            g = 0.25 * np.roll(g, 1, axis=a) + 0.5 * g + 0.25 * np.roll(g, -1, axis=a)
+    return g

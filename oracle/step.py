@@ -26,7 +26,7 @@ class Params:
     """Grid and method parameters (the arguments of the problem statement, Sec. 4 and 5)."""
 
     def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
-                 v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0):
+                 v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0, filter_passes=0):
         self.shape = tuple(int(n) for n in shape)
         self.dx = tuple(float(d) for d in dx)
         self.dt = float(dt)
@@ -37,6 +37,7 @@ class Params:
         self.spectral_order = tuple(int(o) for o in spectral_order)
         self.c = float(c)
         self.eps0 = float(eps0)
+        self.filter_passes = int(filter_passes)
         self._co = None
         self._k = None
 
@@ -100,8 +101,14 @@ def hybrid_step(p, state):
         for a in range(3):
             Jn[a] += J[a]
         rho_np1 += r
-    Jy = [grid.center_to_yee(Jn[a], grid.J_NAMES[a], o) for a in range(3)]             # step 4
-    E, B, avg, im = maxwell_update(p, state["E"], state["B"], Jy, state["rho"], rho_np1)  # step 5
+    # optional smoothing of the deposits (Sec. 2): the solver sees the filtered rho^n, rho^{n+1}
+    # and J; state["rho"] keeps the unfiltered deposit
+    f = p.filter_passes
+    Jf = [grid.bilinear_filter(Jn[a], f) for a in range(3)] if f else Jn
+    rn_f = grid.bilinear_filter(state["rho"], f) if f else state["rho"]
+    rp_f = grid.bilinear_filter(rho_np1, f) if f else rho_np1
+    Jy = [grid.center_to_yee(Jf[a], grid.J_NAMES[a], o) for a in range(3)]             # step 4
+    E, B, avg, im = maxwell_update(p, state["E"], state["B"], Jy, rn_f, rp_f)           # step 5
     state.update(E=E, B=B, J=Jy, rho=rho_np1, species=new_species, max_imag=im)
     if avg is not None:
         state["avg"] = avg

@@ -94,3 +94,29 @@ def test_fft_matches_direct_dft_and_parseval():
                 F[a, b, c] = np.sum(f * ph)
     np.testing.assert_allclose(np.fft.fftn(f), F, atol=1e-13)
     assert abs(np.sum(f ** 2) - np.sum(np.abs(F) ** 2) / f.size) < 1e-12
+
+
+def test_bilinear_filter_symbol_sum_and_stencil():
+    from oracle import grid, fornberg
+    shape = (8, 6, 16)
+    # on a single Fourier mode the filter multiplies by prod_a cos^2(k_a dx_a / 2) per pass
+    rng = np.random.default_rng(2)
+    m = (3, 1, 5)
+    idx = np.indices(shape)
+    phase = sum(2 * np.pi * m[a] * idx[a] / shape[a] for a in range(3))
+    f = np.cos(phase)
+    for passes in (1, 2):
+        sym = np.prod([np.cos(np.pi * m[a] / shape[a]) ** 2 for a in range(3)]) ** passes
+        np.testing.assert_allclose(grid.bilinear_filter(f, passes), sym * f, atol=1e-14)
+    # the sum over the grid is unchanged
+    g = rng.normal(size=shape)
+    assert abs(grid.bilinear_filter(g, 3).sum() - g.sum()) < 1e-12
+    # a delta becomes the outer product of (1/4, 1/2, 1/4)
+    d = np.zeros(shape)
+    d[4, 3, 8] = 1.0
+    h = grid.bilinear_filter(d, 1)
+    w = np.array([0.25, 0.5, 0.25])
+    ref = np.zeros(shape)
+    ref[3:6, 2:5, 7:10] = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    np.testing.assert_allclose(h, ref, atol=1e-16)
+    del fornberg

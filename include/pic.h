@@ -67,6 +67,11 @@ typedef enum {
   PIC_FP32 = 1   /* FP32 form: FP32 fields, particles and FFTs; FP64 coefficient tables and diagnostics */
 } pic_precision;
 
+typedef enum {
+  PIC_PUSHER_BORIS = 0,  /* Boris rotation (the default) */
+  PIC_PUSHER_VAY = 1     /* Vay's pusher, used for the paper's runs (Secs. 5.2-5.3) */
+} pic_pusher;
+
 /*
  * Optional extension block (pass NULL for defaults).  struct_size must be
  * sizeof(pic_ext) of the caller's header (versioning).
@@ -79,6 +84,13 @@ typedef enum {
  *   sort_interval: re-bin the particles every this many steps inside pic_step
  *     (0 = never).  Default 20.
  *   cuda_stream: a cudaStream_t; NULL = legacy default stream.
+ *   filter_passes: passes of the bilinear (1/4, 1/2, 1/4) smoothing filter applied
+ *     along every axis to the deposited J and rho before the field solve (Sec. 2),
+ *     0..8; applied in Fourier space as prod_a cos^2(k_a dx_a / 2) per pass to J,
+ *     rho^n and rho^{n+1} inside the step (the rho array keeps the unfiltered
+ *     deposit; the J written back is the filtered, Yee-centered one).  Default 0.
+ *   pusher: pic_pusher.  Default PIC_PUSHER_BORIS.
+ *   reserved: must be 0.
  */
 typedef struct {
   uint32_t struct_size;
@@ -89,6 +101,9 @@ typedef struct {
   int32_t tile[3];
   int32_t sort_interval;
   void* cuda_stream;
+  int32_t filter_passes;
+  int32_t pusher;
+  int32_t reserved[2];
 } pic_ext;
 
 /* Fill *ext with the defaults listed above. */
@@ -197,7 +212,8 @@ typedef struct {
  *   spbar          per species, in: adjoints of x^{n+1}, u^{n+1/2}; out: of x^n, u^{n-1/2}.
  * The caller keeps checkpoints of the forward state and recomputes each step's
  * state before reversing it (pic_step must then run with sort_interval = 0 so
- * that particle order is stable).  Asynchronous.
+ * that particle order is stable).  PIC_ERR_UNSUPPORTED for the averaged variant,
+ * the Vay pusher and filter_passes > 0.  Asynchronous.
  */
 pic_status pic_adjoint_step(pic_ctx* ctx, const double* const E[3], const double* const B[3],
                             const pic_species* sp, int n_species, double* const Ebar[3], double* const Bbar[3],

@@ -142,7 +142,7 @@ void pic_destroy(pic_ctx* ctx) {
   void* ptrs[] = {ctx->k1d, ctx->twid[0], ctx->twid[1], ctx->twid[2], ctx->coef, ctx->EBh,
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
                   ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work, ctx->bin_gate,
-                  ctx->bin_outside};
+                  ctx->bin_outside, ctx->flt1d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) {
@@ -192,6 +192,9 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   if (psatd_variant < 0 || psatd_variant > 2) return fail(PIC_ERR_ARG, "unknown PSATD variant");
   if (e.precision != PIC_FP64 && e.precision != PIC_FP32) return fail(PIC_ERR_ARG, "precision must be PIC_FP64 or PIC_FP32");
   if (!(e.c > 0.0) || !(e.eps0 > 0.0)) return fail(PIC_ERR_ARG, "c and eps0 must be > 0");
+  if (e.filter_passes < 0 || e.filter_passes > 8) return fail(PIC_ERR_ARG, "filter_passes must be in [0, 8]");
+  if (e.pusher != PIC_PUSHER_BORIS && e.pusher != PIC_PUSHER_VAY) return fail(PIC_ERR_ARG, "unknown pusher");
+  if (e.reserved[0] || e.reserved[1]) return fail(PIC_ERR_ARG, "reserved fields must be 0");
   if (psatd_variant != PIC_PSATD_STANDARD) {
     if (!v_gal) return fail(PIC_ERR_ARG, "v_gal required");
     const double v2 = v_gal[0] * v_gal[0] + v_gal[1] * v_gal[1] + v_gal[2] * v_gal[2];
@@ -212,6 +215,8 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   ctx->eps0 = e.eps0;
   ctx->sort_interval = e.sort_interval;
   ctx->precision = e.precision;
+  ctx->filter_passes = e.filter_passes;
+  ctx->pusher = e.pusher;
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) ctx->sp_off_n[q] = -1;
   ctx->stream = reinterpret_cast<cudaStream_t>(e.cuda_stream);
   ctx->ncell = grid[0] * grid[1] * grid[2];

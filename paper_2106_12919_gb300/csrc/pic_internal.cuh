@@ -84,6 +84,8 @@ struct pic_ctx {
   int tile[3];
   int sort_interval;
   int precision;
+  int filter_passes;  // bilinear smoothing passes of the deposits (0 = off)
+  int pusher;         // pic_pusher
   cudaStream_t stream;
   int64_t ncell, nzh, nmode;
   int ncoef;
@@ -94,6 +96,8 @@ struct pic_ctx {
   double* ks[3];
   double* kc[3];
   double* zeta[3];
+  double* flt1d;     // [3][Nmax] bilinear filter symbols, (cos^2(k dx / 2))^passes; NULL when off
+  double* flt[3];
   double2* twid[3];  // twiddles exp(-2 pi i j / N_a), j < N_a
   float2* twid32[3]; // the same rounded to FP32
   double2* coef;     // [ncoef][nmode]

@@ -247,6 +247,7 @@ struct UpdArgs {
   C* G;                 // [6][nmode] out
   const double* ks[3];
   const double* zt[3];
+  const double* flt[3];  // bilinear filter symbols per axis (NULL: no filter)
   const double2* hs[3];  // half-cell shifts exp(-i k dx / 2)
   int64_t Ny, nzh, nmode;
   double c2;
@@ -275,12 +276,20 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
     B[a] = u.EB[(3 + a) * nm + m];
     J[a] = u.J[a * nm + m];
   }
+  C rn = u.rn[m], rp = u.rp[m];
   if (!u.j_yee) {
     J[0] = cscale(J[0], zx);
     J[1] = cscale(J[1], zy);
     J[2] = cscale(J[2], zz);
+    if (u.flt[0]) {
+      // smoothing of the step's deposits: J^{n+1/2}, rho^n, rho^{n+1}
+      const T f = (T)(u.flt[0][ix] * u.flt[1][iy] * u.flt[2][iz]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) J[a] = cscale(J[a], f);
+      rn = cscale(rn, f);
+      rp = cscale(rp, f);
+    }
   }
-  const C rn = u.rn[m], rp = u.rp[m];
   // [k] x F
   auto cross = [&](const C* F, C* o) {
     o[0] = csub(cscale(F[2], k[1]), cscale(F[1], k[2]));
@@ -605,6 +614,24 @@ pic_status psatd_setup(pic_ctx* ctx) {
     ctx->kc[a] = ctx->k1d + (3 + a) * Nmax;
     ctx->zeta[a] = ctx->k1d + (6 + a) * Nmax;
   }
+  // bilinear filter symbols (Sec. 2): per pass and axis, (1/4, 1/2, 1/4) -> cos^2(k dx / 2)
+  if (ctx->filter_passes > 0) {
+    std::vector<double> hf(3 * Nmax, 0.0);
+    for (int a = 0; a < 3; ++a) {
+      const int64_t N = ctx->N[a];
+      for (int64_t j = 0; j < N; ++j) {
+        const int64_t js = j < N / 2 ? j : j - N;
+        double s, c;
+        sincospi_frac(js, N, &s, &c);  // cos(k dx / 2)
+        double f = 1.0;
+        for (int q = 0; q < ctx->filter_passes; ++q) f *= c * c;
+        hf[a * Nmax + j] = f;
+      }
+    }
+    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->flt1d, 3 * Nmax * sizeof(double)));
+    PIC_CUDA_TRY(ctx, cudaMemcpy(ctx->flt1d, hf.data(), 3 * Nmax * sizeof(double), cudaMemcpyHostToDevice));
+    for (int a = 0; a < 3; ++a) ctx->flt[a] = ctx->flt1d + a * Nmax;
+  }
   // keep the half-cell shift tables right after the 1D tables
   ctx->ncoef = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN ? COEF_COUNT : COEF_PSI1;
   PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->coef, (size_t)ctx->ncoef * ctx->nmode * sizeof(double2)));
@@ -649,6 +676,7 @@ pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C
   for (int a = 0; a < 3; ++a) {
     u.ks[a] = ctx->ks[a];
     u.zt[a] = ctx->zeta[a];
+    u.flt[a] = ctx->filter_passes > 0 ? ctx->flt[a] : nullptr;
     u.hs[a] = half_shift(ctx, a);
   }
   u.Ny = ctx->N[1];

@@ -15,6 +15,7 @@ from . import build as _build
 
 PIC_OK = 0
 PIC_FP64, PIC_FP32 = 0, 1
+PIC_PUSHER_BORIS, PIC_PUSHER_VAY = 0, 1
 STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_UNSUPPORTED", -3: "PIC_ERR_NOMEM",
           -4: "PIC_ERR_CUDA", -5: "PIC_ERR_CAPACITY", -6: "PIC_ERR_TIMEOUT", -7: "PIC_ERR_NONFINITE"}
 STANDARD, GALILEAN, AVERAGED = 0, 1, 2
@@ -28,7 +29,8 @@ _vp = ctypes.c_void_p
 class PicExt(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("spectral_order", _i3), ("precision", ctypes.c_int32),
                 ("c", ctypes.c_double), ("eps0", ctypes.c_double), ("tile", _i3),
-                ("sort_interval", ctypes.c_int32), ("cuda_stream", _vp)]
+                ("sort_interval", ctypes.c_int32), ("cuda_stream", _vp), ("filter_passes", ctypes.c_int32),
+                ("pusher", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class PicSpecies(ctypes.Structure):
@@ -241,7 +243,8 @@ class Context:
 
     def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
                  v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0,
-                 tile=(4, 8, 8), sort_interval=20, stream=None, precision=PIC_FP64):
+                 tile=(4, 8, 8), sort_interval=20, stream=None, precision=PIC_FP64, filter_passes=0,
+                 pusher=0):
         self.shape = tuple(int(n) for n in shape)
         self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
         self.nmode = self.shape[0] * self.shape[1] * (self.shape[2] // 2 + 1)
@@ -256,6 +259,8 @@ class Context:
         ext.tile = _i3(*tile)
         ext.sort_interval = sort_interval
         ext.precision = precision
+        ext.filter_passes = filter_passes
+        ext.pusher = pusher
         self.precision = precision
         ext.cuda_stream = self.stream.cuda_stream
         h = _vp()

@@ -150,6 +150,8 @@ CASES = [
     # a dense driver: its central tiles hold up to ~5000 particles, so the tiled push
     # splits them into chunks of at most 2048 that deposit into the same tile window
     ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=100000), 20, False),
+    # bilinear smoothing of the deposits (Sec. 2)
+    ("laser_wakefield:filter2", dict(shape=(16, 16, 64), ppc=1), 100, False),
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 100, True),
     ("galilean_drift", dict(shape=(16, 16, 32), ppc=1), 100, True),
 ]
@@ -183,12 +185,14 @@ def _oracle_run(op, E, B, species, nsteps, noise=None):
 @pytest.mark.parametrize("name,kw,nsteps,chaotic", CASES)
 def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
     import torch
+    name, _, opt = name.partition(":")
+    opts = {"filter_passes": int(opt[len("filter"):])} if opt.startswith("filter") else {}
     w = workloads.WORKLOADS[name](**kw)
     p = w["params"]
     shape, dx = p["shape"], p["dx"]
-    ctx = ctx32(p, sort_interval=10)
+    ctx = ctx32(p, sort_interval=10, **opts)
     sp = species32(w["species"], shape, dx)
-    op = step.Params(**p)
+    op = step.Params(**p, **opts)
     E0 = [a.astype(np.float32).astype(np.float64) for a in w["E"]]
     B0 = [a.astype(np.float32).astype(np.float64) for a in w["B"]]
     sp0 = as_oracle_species(sp, shape, dx)

@@ -105,14 +105,45 @@ def boris(u, E, B, q, m, dt, c=1.0):
     return [upl[a] + k * E[a] for a in range(3)]
 
 
+def vay(u, E, B, q, m, dt, c=1.0):
+    """Vay's pusher (J.-L. Vay, Phys. Plasmas 15, 056701 (2008); used for the paper's runs,
+    Secs. 5.2-5.3): u^{n+1/2} - u^{n-1/2} = (q dt / m) (E + vbar x B) with vbar the mean of
+    v^{n-1/2} and v^{n+1/2}, v = u / gamma, solved in closed form for u^{n+1/2}:
+      u' = u + (q dt / m) (E + (v^{n-1/2} x B) / 2),   tau = (q dt / (2 m)) B,
+      gamma^2 solves gamma^4 - sigma gamma^2 - (tau^2 + (u'.tau / c)^2) = 0,
+      sigma = 1 + u'^2 / c^2 - tau^2,
+      t = tau / gamma,  u^{n+1/2} = (u' + (u'.t) t + u' x t) / (1 + t^2).
+    """
+    g0 = np.sqrt(1.0 + (u[0] ** 2 + u[1] ** 2 + u[2] ** 2) / (c * c))
+    v0 = [u[a] / g0 for a in range(3)]
+    k = q * dt / m
+    vxB = [v0[1] * B[2] - v0[2] * B[1], v0[2] * B[0] - v0[0] * B[2], v0[0] * B[1] - v0[1] * B[0]]
+    up = [u[a] + k * (E[a] + 0.5 * vxB[a]) for a in range(3)]
+    tau = [0.5 * k * B[a] for a in range(3)]
+    tau2 = tau[0] ** 2 + tau[1] ** 2 + tau[2] ** 2
+    ustar = (up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2]) / c
+    sigma = 1.0 + (up[0] ** 2 + up[1] ** 2 + up[2] ** 2) / (c * c) - tau2
+    gam = np.sqrt(0.5 * (sigma + np.sqrt(sigma * sigma + 4.0 * (tau2 + ustar * ustar))))
+    t = [tau[a] / gam for a in range(3)]
+    s = 1.0 / (1.0 + t[0] ** 2 + t[1] ** 2 + t[2] ** 2)
+    ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2]
+    uxt = [up[1] * t[2] - up[2] * t[1], up[2] * t[0] - up[0] * t[2], up[0] * t[1] - up[1] * t[0]]
+    return [s * (up[a] + ut * t[a] + uxt[a]) for a in range(3)]
+
+
+PUSHERS = {0: boris, 1: vay}
+
+
 def wrap(x, L):
     """Periodic wrap of a position that moved by less than one box length."""
     x = np.where(x >= L, x - L, x)
     return np.where(x < 0.0, x + L, x)
 
 
-def push_and_deposit(sp, nodal_E, nodal_B, grid_shape, dx, dt, order, v_gal=(0.0, 0.0, 0.0), c=1.0):
-    """Gather at x^n, Boris push, move, and deposit J^{n+1/2} and rho^{n+1} for one species.
+def push_and_deposit(sp, nodal_E, nodal_B, grid_shape, dx, dt, order, v_gal=(0.0, 0.0, 0.0), c=1.0,
+                     pusher=0):
+    """Gather at x^n, push (Boris, or Vay with pusher = 1), move, and deposit J^{n+1/2} and
+    rho^{n+1} for one species.
 
     sp: dict with x, y, z, ux, uy, uz, w (float64 arrays) and q, m (floats).
     Returns (new species dict, [Jx, Jy, Jz] nodal, rho nodal).
@@ -121,7 +152,7 @@ def push_and_deposit(sp, nodal_E, nodal_B, grid_shape, dx, dt, order, v_gal=(0.0
     pos = [sp["x"], sp["y"], sp["z"]]
     E = gather(nodal_E, pos, dx, order)
     B = gather(nodal_B, pos, dx, order)
-    u = boris([sp["ux"], sp["uy"], sp["uz"]], E, B, sp["q"], sp["m"], dt, c)
+    u = PUSHERS[pusher]([sp["ux"], sp["uy"], sp["uz"]], E, B, sp["q"], sp["m"], dt, c)
     g = np.sqrt(1.0 + (u[0] ** 2 + u[1] ** 2 + u[2] ** 2) / (c * c))
     v = [u[a] / g for a in range(3)]
     mid = [wrap(pos[a] + 0.5 * dt * (v[a] - v_gal[a]), L[a]) for a in range(3)]

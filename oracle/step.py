@@ -26,7 +26,8 @@ class Params:
     """Grid and method parameters (the arguments of the problem statement, Sec. 4 and 5)."""
 
     def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
-                 v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0, filter_passes=0):
+                 v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0, filter_passes=0,
+                 pusher=0):
         self.shape = tuple(int(n) for n in shape)
         self.dx = tuple(float(d) for d in dx)
         self.dt = float(dt)
@@ -38,6 +39,7 @@ class Params:
         self.c = float(c)
         self.eps0 = float(eps0)
         self.filter_passes = int(filter_passes)
+        self.pusher = int(pusher)        # 0: Boris, 1: Vay
         self._co = None
         self._k = None
 
@@ -96,7 +98,7 @@ def hybrid_step(p, state):
     new_species = []
     for sp in state["species"]:                                                       # steps 2-3
         nsp, J, r = particles.push_and_deposit(sp, nE, nB, p.shape, p.dx, p.dt, p.shape_order,
-                                               p.v_gal, p.c)
+                                               p.v_gal, p.c, p.pusher)
         new_species.append(nsp)
         for a in range(3):
             Jn[a] += J[a]

@@ -95,3 +95,50 @@ def test_tile_bins_brute_force():
         assert tid[p] == ((c[0] // tile[0]) * nt[1] + c[1] // tile[1]) * nt[2] + c[2] // tile[2]
     assert off[0] == 0 and off[-1] == 4000 and len(off) == nt[0] * nt[1] * nt[2] + 1
     assert np.all(np.diff(tid[order]) >= 0)
+
+
+def test_vay_solves_its_defining_equation():
+    # (u^{n+1/2} - u^{n-1/2}) m / (q dt) = E + (v^{n-1/2} + v^{n+1/2}) / 2 x B, v = u / gamma
+    from oracle import particles
+    rng = np.random.default_rng(11)
+    n = 200
+    c, q, m, dt = 2.0, -1.5, 0.7, 0.3
+    u = [rng.normal(0, 3.0, n) for _ in range(3)]
+    E = [rng.normal(0, 2.0, n) for _ in range(3)]
+    B = [rng.normal(0, 2.0, n) for _ in range(3)]
+    un = particles.vay(u, E, B, q, m, dt, c)
+    gam = lambda w: np.sqrt(1.0 + (w[0] ** 2 + w[1] ** 2 + w[2] ** 2) / (c * c))
+    g0, g1 = gam(u), gam(un)
+    vb = [0.5 * (u[a] / g0 + un[a] / g1) for a in range(3)]
+    rhs = [E[0] + vb[1] * B[2] - vb[2] * B[1], E[1] + vb[2] * B[0] - vb[0] * B[2],
+           E[2] + vb[0] * B[1] - vb[1] * B[0]]
+    for a in range(3):
+        lhs = (un[a] - u[a]) * m / (q * dt)
+        np.testing.assert_allclose(lhs, rhs[a], rtol=1e-11, atol=1e-11)
+
+
+def test_vay_keeps_the_exb_drift_exactly_and_boris_does_not():
+    # E = E0 y, B = B0 z: the drift v_d = E x B / B^2 = (E0 / B0) x sees no force
+    from oracle import particles
+    c, q, m, dt = 1.0, -1.0, 1.0, 0.5
+    E0, B0 = 0.999 * 20.0, 20.0
+    vd = E0 / B0
+    gd = 1.0 / np.sqrt(1.0 - vd * vd)
+    u = [np.array([gd * vd]), np.array([0.0]), np.array([0.0])]
+    E = [np.array([0.0]), np.array([E0]), np.array([0.0])]
+    B = [np.array([0.0]), np.array([0.0]), np.array([B0])]
+    uv = particles.vay(u, E, B, q, m, dt, c)
+    ub = particles.boris(u, E, B, q, m, dt, c)
+    assert abs(uv[0][0] - u[0][0]) < 1e-12 * u[0][0] and abs(uv[1][0]) < 1e-12 * u[0][0]
+    assert abs(ub[0][0] - u[0][0]) + abs(ub[1][0]) > 1e-3 * u[0][0]
+
+
+def test_vay_pure_electric_kick():
+    from oracle import particles
+    rng = np.random.default_rng(5)
+    u = [rng.normal(size=10) for _ in range(3)]
+    E = [rng.normal(size=10) for _ in range(3)]
+    Z = [np.zeros(10)] * 3
+    un = particles.vay(u, E, Z, 2.0, 0.5, 0.1, 1.0)
+    for a in range(3):
+        np.testing.assert_allclose(un[a], u[a] + 2.0 / 0.5 * 0.1 * E[a], rtol=1e-14, atol=1e-14)

@@ -31,6 +31,7 @@ struct PushArgs {
   double vg[3];
   double qw_scale;     // q / dV
   int gather;          // 0: rho-only deposit at the current position
+  int vay;             // 1: Vay's pusher instead of Boris
 };
 
 template <int P>
@@ -115,19 +116,27 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
       }
     }
   }
-  // Boris push u^{n-1/2} -> u^{n+1/2}
+  // push u^{n-1/2} -> u^{n+1/2}
   const double k = a.qm_half_dt;
-  const double umx = a.ux[p] + k * f[0], umy = a.uy[p] + k * f[1], umz = a.uz[p] + k * f[2];
-  const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
-  const double tx = k * f[3] / gm, ty = k * f[4] / gm, tz = k * f[5] / gm;
-  const double s2 = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
-  const double sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
-  const double upx = umx + (umy * tz - umz * ty);
-  const double upy = umy + (umz * tx - umx * tz);
-  const double upz = umz + (umx * ty - umy * tx);
-  const double ux = umx + (upy * sz - upz * sy) + k * f[0];
-  const double uy = umy + (upz * sx - upx * sz) + k * f[1];
-  const double uz = umz + (upx * sy - upy * sx) + k * f[2];
+  double ux, uy, uz;
+  if (a.vay) {
+    ux = a.ux[p];
+    uy = a.uy[p];
+    uz = a.uz[p];
+    vay_push<double>(ux, uy, uz, f, k, a.inv_c2);
+  } else {  // Boris
+    const double umx = a.ux[p] + k * f[0], umy = a.uy[p] + k * f[1], umz = a.uz[p] + k * f[2];
+    const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
+    const double tx = k * f[3] / gm, ty = k * f[4] / gm, tz = k * f[5] / gm;
+    const double s2 = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
+    const double sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+    const double upx = umx + (umy * tz - umz * ty);
+    const double upy = umy + (umz * tx - umx * tz);
+    const double upz = umz + (umx * ty - umy * tx);
+    ux = umx + (upy * sz - upz * sy) + k * f[0];
+    uy = umy + (upz * sx - upx * sz) + k * f[1];
+    uz = umz + (upx * sy - upy * sx) + k * f[2];
+  }
   const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
   const double vx = ux * ig, vy = uy * ig, vz = uz * ig;
   // move: x^{n+1} = x^n + dt (v - v_gal); J at x^{n+1/2}
@@ -200,6 +209,7 @@ PushArgs make_args(pic_ctx* ctx, const pic_species* sp) {
   a.qm_half_dt = sp->q * ctx->dt / (2.0 * sp->m);
   a.dt = ctx->dt;
   a.inv_c2 = 1.0 / (ctx->c * ctx->c);
+  a.vay = ctx->pusher == PIC_PUSHER_VAY ? 1 : 0;
   a.qw_scale = sp->q / (ctx->dx[0] * ctx->dx[1] * ctx->dx[2]);
   return a;
 }

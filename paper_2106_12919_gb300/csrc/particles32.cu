@@ -30,6 +30,7 @@ struct Push32Args {
   float vg[3];
   float qw_scale;     // q / dV
   int gather;
+  int vay;            // 1: Vay's pusher instead of Boris
 };
 
 // shape of order P from the base cell i and the offset f in [0, 1)
@@ -56,6 +57,30 @@ __device__ __forceinline__ void shape32(int i, float f, int& lo, float* S) {
     S[2] = (1.0f + 3.0f * f + 3.0f * d2 - 3.0f * d3) * (1.0f / 6.0f);
     S[3] = d3 * (1.0f / 6.0f);
   }
+}
+
+// u^{n-1/2} of particle p -> u^{n+1/2} with the gathered f = (E, B): Boris rotation, or Vay's pusher
+__device__ __forceinline__ void push_u(const Push32Args& a, int64_t p, const float* f, float& ux, float& uy,
+                                       float& uz) {
+  const float kq = a.qm_half_dt;
+  if (a.vay) {
+    ux = a.ux[p];
+    uy = a.uy[p];
+    uz = a.uz[p];
+    vay_push<float>(ux, uy, uz, f, kq, a.inv_c2);
+    return;
+  }
+  const float umx = a.ux[p] + kq * f[0], umy = a.uy[p] + kq * f[1], umz = a.uz[p] + kq * f[2];
+  const float igm = rsqrtf(1.0f + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
+  const float tx = kq * f[3] * igm, ty = kq * f[4] * igm, tz = kq * f[5] * igm;
+  const float s2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+  const float sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+  const float upx = umx + (umy * tz - umz * ty);
+  const float upy = umy + (umz * tx - umx * tz);
+  const float upz = umz + (umx * ty - umy * tx);
+  ux = umx + (upy * sz - upz * sy) + kq * f[0];
+  uy = umy + (upz * sx - upx * sz) + kq * f[1];
+  uz = umz + (upx * sy - upy * sx) + kq * f[2];
 }
 
 // offset f moved by d cells: new (cell shift, offset in [0, 1))
@@ -219,19 +244,9 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
       }
     }
   }
-  // Boris push u^{n-1/2} -> u^{n+1/2}
-  const float kq = a.qm_half_dt;
-  const float umx = a.ux[p] + kq * f[0], umy = a.uy[p] + kq * f[1], umz = a.uz[p] + kq * f[2];
-  const float igm = rsqrtf(1.0f + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
-  const float tx = kq * f[3] * igm, ty = kq * f[4] * igm, tz = kq * f[5] * igm;
-  const float s2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
-  const float sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
-  const float upx = umx + (umy * tz - umz * ty);
-  const float upy = umy + (umz * tx - umx * tz);
-  const float upz = umz + (umx * ty - umy * tx);
-  const float ux = umx + (upy * sz - upz * sy) + kq * f[0];
-  const float uy = umy + (upz * sx - upx * sz) + kq * f[1];
-  const float uz = umz + (upx * sy - upy * sx) + kq * f[2];
+  // push u^{n-1/2} -> u^{n+1/2}
+  float ux, uy, uz;
+  push_u(a, p, f, ux, uy, uz);
   const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
   const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
   // displacement in cells
@@ -399,18 +414,8 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
       }
       ++nout;
     }
-    const float kq = a.qm_half_dt;
-    const float umx = a.ux[p] + kq * f[0], umy = a.uy[p] + kq * f[1], umz = a.uz[p] + kq * f[2];
-    const float igm = rsqrtf(1.0f + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
-    const float tx_ = kq * f[3] * igm, ty_ = kq * f[4] * igm, tz_ = kq * f[5] * igm;
-    const float s2 = 2.0f / (1.0f + tx_ * tx_ + ty_ * ty_ + tz_ * tz_);
-    const float sx = s2 * tx_, sy = s2 * ty_, sz = s2 * tz_;
-    const float upx = umx + (umy * tz_ - umz * ty_);
-    const float upy = umy + (umz * tx_ - umx * tz_);
-    const float upz = umz + (umx * ty_ - umy * tx_);
-    const float ux = umx + (upy * sz - upz * sy) + kq * f[0];
-    const float uy = umy + (upz * sx - upx * sz) + kq * f[1];
-    const float uz = umz + (upx * sy - upy * sx) + kq * f[2];
+    float ux, uy, uz;
+    push_u(a, p, f, ux, uy, uz);
     const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
     const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
     const float dX = a.dtdx[0] * (vx - a.vg[0]), dY = a.dtdx[1] * (vy - a.vg[1]), dZ = a.dtdx[2] * (vz - a.vg[2]);
@@ -538,6 +543,7 @@ Push32Args make_args32(pic_ctx* ctx, const pic_species32* sp) {
   a.Nz = ctx->N[2];
   a.qm_half_dt = (float)(sp->q * ctx->dt / (2.0 * sp->m));
   a.inv_c2 = (float)(1.0 / (ctx->c * ctx->c));
+  a.vay = ctx->pusher == PIC_PUSHER_VAY ? 1 : 0;
   a.qw_scale = (float)(sp->q / (ctx->dx[0] * ctx->dx[1] * ctx->dx[2]));
   return a;
 }

@@ -209,6 +209,39 @@ pic_status psatd_adjoint_update(pic_ctx* ctx, double2* EB, double2* G);
 // EB[c] += zeta_c * src[c] (c = 0..5): transpose of the E, B -> nodal centering.
 pic_status psatd_add_zeta(pic_ctx* ctx, double2* EB, const double2* src);
 
+// Vay's pusher (J.-L. Vay, Phys. Plasmas 15, 056701 (2008); the pusher of the paper's runs,
+// Secs. 5.2-5.3): u^{n+1/2} - u^{n-1/2} = (q dt / m) (E + vbar x B), vbar the mean of v^{n-1/2}
+// and v^{n+1/2}, v = u / gamma, solved in closed form:
+//   u' = u + (q dt / m) (E + (v^{n-1/2} x B) / 2),  tau = (q dt / (2 m)) B,
+//   gamma^2 = root of gamma^4 - sigma gamma^2 - (tau^2 + (u'.tau)^2 / c^2),  sigma = 1 + u'^2 / c^2 - tau^2,
+//   t = tau / gamma,  u^{n+1/2} = (u' + (u'.t) t + u' x t) / (1 + t^2).
+// The positive root is taken as (sigma + R)/2 for sigma >= 0 and as 2 b / (R - sigma) for
+// sigma < 0 (R = sqrt(sigma^2 + 4 b), b = tau^2 + (u'.tau)^2 / c^2): equal in exact
+// arithmetic, the second avoids cancellation.  k = q dt / (2 m); f = (E, B) at the particle.
+template <class T>
+__device__ __forceinline__ void vay_push(T& ux, T& uy, T& uz, const T* f, T k, T inv_c2) {
+  const T ig0 = T(1) / sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * inv_c2);
+  const T vx = ux * ig0, vy = uy * ig0, vz = uz * ig0;
+  const T k2 = k + k;
+  const T upx = ux + k2 * f[0] + k * (vy * f[5] - vz * f[4]);
+  const T upy = uy + k2 * f[1] + k * (vz * f[3] - vx * f[5]);
+  const T upz = uz + k2 * f[2] + k * (vx * f[4] - vy * f[3]);
+  const T tx = k * f[3], ty = k * f[4], tz = k * f[5];
+  const T tau2 = tx * tx + ty * ty + tz * tz;
+  const T us = upx * tx + upy * ty + upz * tz;
+  const T b = tau2 + us * us * inv_c2;
+  const T sigma = T(1) + (upx * upx + upy * upy + upz * upz) * inv_c2 - tau2;
+  const T R = sqrt(sigma * sigma + T(4) * b);
+  const T g2 = sigma >= T(0) ? T(0.5) * (sigma + R) : T(2) * b / (R - sigma);
+  const T ig = T(1) / sqrt(g2);
+  const T qx = tx * ig, qy = ty * ig, qz = tz * ig;
+  const T sn = T(1) / (T(1) + qx * qx + qy * qy + qz * qz);
+  const T ut = upx * qx + upy * qy + upz * qz;
+  ux = sn * (upx + ut * qx + (upy * qz - upz * qy));
+  uy = sn * (upy + ut * qy + (upz * qx - upx * qz));
+  uz = sn * (upz + ut * qz + (upx * qy - upy * qx));
+}
+
 // index of a coefficient table by name ("TC", "TS", ..., see pic_coefficient), -1 if unknown
 int coef_index(const pic_ctx* ctx, const char* name);
 

@@ -152,6 +152,9 @@ CASES = [
     ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=100000), 20, False),
     # bilinear smoothing of the deposits (Sec. 2)
     ("laser_wakefield:filter2", dict(shape=(16, 16, 64), ppc=1), 100, False),
+    # Vay's pusher
+    ("laser_wakefield:vay", dict(shape=(16, 16, 64), ppc=1), 100, False),
+    ("beam_wakefield:vay", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 100, False),
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 100, True),
     ("galilean_drift", dict(shape=(16, 16, 32), ppc=1), 100, True),
 ]
@@ -187,6 +190,8 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
     import torch
     name, _, opt = name.partition(":")
     opts = {"filter_passes": int(opt[len("filter"):])} if opt.startswith("filter") else {}
+    if opt == "vay":
+        opts = {"pusher": 1}
     w = workloads.WORKLOADS[name](**kw)
     p = w["params"]
     shape, dx = p["shape"], p["dx"]

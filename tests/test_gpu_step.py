@@ -29,6 +29,10 @@ CASES = [
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 4, {"filter_passes": 1}),
     ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, {"filter_passes": 2}),
     ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 3, {"filter_passes": 1}),
+    # Vay's pusher (the paper's runs, Secs. 5.2-5.3)
+    ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, {"pusher": 1}),
+    ("galilean_electrons", dict(shape=(16, 16, 32), ppc=1), 3, {"pusher": 1}),
+    ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 3, {"pusher": 1, "filter_passes": 1}),
 ]
 
 

@@ -45,14 +45,18 @@ def _b3(v, a):
 
 
 def coefficients(shape, dx, dt, spectral_order, v_gal=(0.0, 0.0, 0.0), c=1.0, eps0=1.0,
-                 averaged=False):
+                 averaged=False, nodal=False):
     """Per-mode update coefficients, complex128 arrays of the full spectrum shape.
 
     Keys: 'TC' = theta_c^2 C, 'TS' = theta_c^2 S/omega_s, 'X1', 'X2', 'TX3' = theta_c^2 X3,
     'X4' (Secs. 4.2-4.3; theta_c = 1 when v_gal = 0) and, if averaged,
     'Psi1', 'Psi2', 'Y1', 'Y2', 'Y3', 'Y4' (Sec. 4.4).
+    nodal: the nodal solver of the comparison cycle (Sec. 2), in which every quantity lives on
+    the nodes and the centered modified wave numbers replace [k]_s (omega = c |[k]_c|).
     """
     ks, kc = modified_wave_vectors(shape, dx, spectral_order)
+    if nodal:
+        ks = kc = nodal_k(shape, kc, spectral_order)
     c = LD(c)
     eps0 = LD(eps0)
     dt = LD(dt)
@@ -117,10 +121,26 @@ def coefficients(shape, dx, dt, spectral_order, v_gal=(0.0, 0.0, 0.0), c=1.0, ep
     return {k: np.asarray(v, dtype=CLD).astype(np.complex128) for k, v in out.items()}
 
 
-def staggered_k_grid(shape, dx, spectral_order):
-    """The three components of [k]_s broadcast to the spectrum shape, float64."""
-    ks, _ = modified_wave_vectors(shape, dx, spectral_order)
-    return [np.broadcast_to(_b3(ks[a].astype(np.float64), a), shape) for a in range(3)]
+def nodal_k(shape, kc, spectral_order):
+    """[k]_c of the nodal solver: at infinite order its Nyquist entry (signed index -N/2) is
+    set to 0, the centered derivative of a node-based field there (at finite order the sum of
+    Eq. centered_modified_wave_number already gives 0); otherwise i [k]_c would break the
+    Hermitian symmetry of real fields on the Nyquist planes."""
+    out = []
+    for a in range(3):
+        k = kc[a].copy()
+        if spectral_order[a] == 0 and shape[a] % 2 == 0:
+            k[shape[a] // 2] = 0
+        out.append(k)
+    return out
+
+
+def staggered_k_grid(shape, dx, spectral_order, nodal=False):
+    """The three components of [k]_s (nodal: [k]_c, see nodal_k) broadcast to the spectrum
+    shape, float64."""
+    ks, kc = modified_wave_vectors(shape, dx, spectral_order)
+    k = nodal_k(shape, kc, spectral_order) if nodal else ks
+    return [np.broadcast_to(_b3(k[a].astype(np.float64), a), shape) for a in range(3)]
 
 
 def cross(k, F):

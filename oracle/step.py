@@ -10,6 +10,9 @@ One step, in the paper's order:
   5. solve Maxwell's equations on the Yee grid in Fourier space (Sec. 4): forward
      transforms, PSATD update, inverse transforms.
 
+Nodal comparison cycle (Sec. 2, the "standard" PSATD PIC cycle on a nodal grid): every
+quantity on the nodes, the centered modified wave numbers [k]_c in the solver, no centering.
+
 Averaged Galilean variant (Sec. 4.4): the Yee state E, B evolves with the
 Galilean update; the averaged fields <E>^{n+1}, <B>^{n+1} computed alongside are
 what the next step gathers (they replace E, B in step 1).  The first step gathers
@@ -20,6 +23,7 @@ import numpy as np
 from . import grid, particles, psatd
 
 STANDARD, GALILEAN, AVERAGED = 0, 1, 2
+HYBRID, NODAL = 0, 1
 
 
 class Params:
@@ -27,7 +31,7 @@ class Params:
 
     def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
                  v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0, filter_passes=0,
-                 pusher=0):
+                 pusher=0, cycle=HYBRID):
         self.shape = tuple(int(n) for n in shape)
         self.dx = tuple(float(d) for d in dx)
         self.dt = float(dt)
@@ -40,15 +44,17 @@ class Params:
         self.eps0 = float(eps0)
         self.filter_passes = int(filter_passes)
         self.pusher = int(pusher)        # 0: Boris, 1: Vay
+        self.cycle = int(cycle)          # HYBRID (Sec. 2) or the fully NODAL comparison cycle
         self._co = None
         self._k = None
 
     def coefficients(self):
         if self._co is None:
+            nodal = self.cycle == NODAL
             self._co = psatd.coefficients(self.shape, self.dx, self.dt, self.spectral_order,
                                           self.v_gal, self.c, self.eps0,
-                                          averaged=self.variant == AVERAGED)
-            self._k = psatd.staggered_k_grid(self.shape, self.dx, self.spectral_order)
+                                          averaged=self.variant == AVERAGED, nodal=nodal)
+            self._k = psatd.staggered_k_grid(self.shape, self.dx, self.spectral_order, nodal=nodal)
         return self._co, self._k
 
 
@@ -58,25 +64,29 @@ def maxwell_update(p, E, B, J, rho_n, rho_np1):
     Returns (E, B, avg or None, max |Im| seen in the inverse transforms).
     """
     co, k = p.coefficients()
-    Eh = [grid.to_spectral(E[a], grid.E_NAMES[a], p.dx) for a in range(3)]
-    Bh = [grid.to_spectral(B[a], grid.B_NAMES[a], p.dx) for a in range(3)]
-    Jh = [grid.to_spectral(J[a], grid.J_NAMES[a], p.dx) for a in range(3)]
+    # positions of the components: the Yee grid, or the nodes in the nodal cycle
+    nE = grid.E_NAMES if p.cycle == HYBRID else ("rho",) * 3
+    nB = grid.B_NAMES if p.cycle == HYBRID else ("rho",) * 3
+    nJ = grid.J_NAMES if p.cycle == HYBRID else ("rho",) * 3
+    Eh = [grid.to_spectral(E[a], nE[a], p.dx) for a in range(3)]
+    Bh = [grid.to_spectral(B[a], nB[a], p.dx) for a in range(3)]
+    Jh = [grid.to_spectral(J[a], nJ[a], p.dx) for a in range(3)]
     rn = grid.to_spectral(rho_n, "rho", p.dx)
     rp = grid.to_spectral(rho_np1, "rho", p.dx)
     En, Bn = psatd.update(Eh, Bh, Jh, rn, rp, co, k, p.c)
     im = 0.0
     Eo, Bo = [], []
     for a in range(3):
-        f, i1 = grid.from_spectral(En[a], grid.E_NAMES[a], p.dx)
-        g, i2 = grid.from_spectral(Bn[a], grid.B_NAMES[a], p.dx)
+        f, i1 = grid.from_spectral(En[a], nE[a], p.dx)
+        g, i2 = grid.from_spectral(Bn[a], nB[a], p.dx)
         Eo.append(f)
         Bo.append(g)
         im = max(im, i1, i2)
     avg = None
     if p.variant == AVERAGED:
         Ea, Ba = psatd.update_averaged(Eh, Bh, Jh, rn, rp, co, k, p.c)
-        avg = ([grid.from_spectral(Ea[a], grid.E_NAMES[a], p.dx)[0] for a in range(3)],
-               [grid.from_spectral(Ba[a], grid.B_NAMES[a], p.dx)[0] for a in range(3)])
+        avg = ([grid.from_spectral(Ea[a], nE[a], p.dx)[0] for a in range(3)],
+               [grid.from_spectral(Ba[a], nB[a], p.dx)[0] for a in range(3)])
     return Eo, Bo, avg, im
 
 
@@ -91,8 +101,11 @@ def hybrid_step(p, state):
     if p.variant == AVERAGED and state.get("avg") is not None:
         gE, gB = state["avg"]
     o = p.centering_order
-    nE = [grid.center_to_nodal(gE[a], grid.E_NAMES[a], o) for a in range(3)]          # step 1
-    nB = [grid.center_to_nodal(gB[a], grid.B_NAMES[a], o) for a in range(3)]
+    if p.cycle == NODAL:          # nodal comparison cycle: E, B already live on the nodes
+        nE, nB = [np.asarray(f) for f in gE], [np.asarray(f) for f in gB]
+    else:
+        nE = [grid.center_to_nodal(gE[a], grid.E_NAMES[a], o) for a in range(3)]      # step 1
+        nB = [grid.center_to_nodal(gB[a], grid.B_NAMES[a], o) for a in range(3)]
     Jn = [np.zeros(p.shape) for _ in range(3)]
     rho_np1 = np.zeros(p.shape)
     new_species = []
@@ -109,7 +122,10 @@ def hybrid_step(p, state):
     Jf = [grid.bilinear_filter(Jn[a], f) for a in range(3)] if f else Jn
     rn_f = grid.bilinear_filter(state["rho"], f) if f else state["rho"]
     rp_f = grid.bilinear_filter(rho_np1, f) if f else rho_np1
-    Jy = [grid.center_to_yee(Jf[a], grid.J_NAMES[a], o) for a in range(3)]             # step 4
+    if p.cycle == NODAL:
+        Jy = Jf
+    else:
+        Jy = [grid.center_to_yee(Jf[a], grid.J_NAMES[a], o) for a in range(3)]         # step 4
     E, B, avg, im = maxwell_update(p, state["E"], state["B"], Jy, rn_f, rp_f)           # step 5
     state.update(E=E, B=B, J=Jy, rho=rho_np1, species=new_species, max_imag=im)
     if avg is not None:

@@ -96,3 +96,56 @@ def test_cold_plasma_oscillation_at_plasma_frequency():
     period = 2 * np.mean(np.diff(crossings))
     omega = 2 * np.pi / period
     assert abs(omega - 1.0) < 0.03
+
+
+@pytest.mark.parametrize("variant,order,v", [(0, (8, 8, 8), 0.0), (1, (16, 16, 16), 0.9)])
+def test_nodal_cycle_vacuum_energy_conserved(variant, order, v):
+    # the nodal comparison cycle (Sec. 2): all quantities on the nodes, [k]_c in the solver
+    shape, dx, dt = (8, 8, 16), (1.0, 0.8, 0.5), 0.45
+    p = step.Params(shape, dx, dt, 1, (8, 8, 8), variant, (0.0, 0.0, v), order, cycle=step.NODAL)
+    rng = np.random.default_rng(1)
+    k = psatd.staggered_k_grid(shape, dx, order, nodal=True)
+    k2 = sum(k[a] ** 2 for a in range(3))
+    k2s = np.where(k2 == 0, 1.0, k2)
+
+    def solenoidal():
+        F = [np.fft.fftn(rng.normal(size=shape)) for _ in range(3)]
+        kd = sum(k[a] * F[a] for a in range(3)) / k2s
+        return [np.fft.ifftn(F[a] - k[a] * kd).real for a in range(3)]
+
+    st = {"E": solenoidal(), "B": solenoidal(), "species": [], "rho": np.zeros(shape)}
+    W0 = diagnostics.field_energy(st["E"], st["B"], dx)
+    for _ in range(40):
+        step.hybrid_step(p, st)
+    W1 = diagnostics.field_energy(st["E"], st["B"], dx)
+    assert abs(W1 - W0) < 1e-12 * W0
+
+
+def test_nodal_and_staggered_dispersion_at_nyquist():
+    # Sec. 2 (i): at finite order the nodal solver's vacuum waves stand still at the Nyquist
+    # wave number ([k]_c = 0 there), the staggered solver's do not; omega = c |[k]_c| / c |[k]_s|
+    from oracle import fornberg
+    shape, dx, dt, order = (4, 4, 32), (1.0, 1.0, 1.0), 0.5, (16, 16, 16)
+    N = shape[2]
+    for nodal in (False, True):
+        co = psatd.coefficients(shape, dx, dt, order, nodal=nodal)
+        kk = psatd.staggered_k_grid(shape, dx, order, nodal=nodal)
+        w = diagnostics.vacuum_dispersion(co, kk, 2, 1.0, dt)
+        ref = fornberg.k_centered(N, 1.0, 16) if nodal else fornberg.k_staggered(N, 1.0, 16)
+        np.testing.assert_allclose(w, np.abs(np.asarray(ref, np.float64)), rtol=1e-12, atol=1e-13)
+        nyq = N // 2
+        assert (w[nyq] < 1e-12) if nodal else (w[nyq] > 1.0)
+
+
+def test_nodal_cycle_charge_conserved():
+    w = workloads.thermal_plasma(shape=(8, 8, 8), ppc=2)
+    p = step.Params(**w["params"], cycle=step.NODAL)
+    st = {"E": [a.copy() for a in w["E"]], "B": [a.copy() for a in w["B"]],
+          "species": [dict(s) for s in w["species"]]}
+    st["rho"] = step.initial_rho(p, st["species"])
+    qtot = sum(float(np.sum(s["q"] * s["w"])) for s in st["species"])
+    qabs = sum(float(np.sum(np.abs(s["q"] * s["w"]))) for s in st["species"])
+    for _ in range(3):
+        step.hybrid_step(p, st)
+        assert abs(np.sum(st["rho"]) * np.prod(p.dx) - qtot) < 1e-12 * qabs
+        assert st["max_imag"] < 1e-9 * max(1.0, max(np.abs(e).max() for e in st["E"]))

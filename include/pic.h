@@ -72,6 +72,12 @@ typedef enum {
   PIC_PUSHER_VAY = 1     /* Vay's pusher, used for the paper's runs (Secs. 5.2-5.3) */
 } pic_pusher;
 
+typedef enum {
+  PIC_CYCLE_HYBRID = 0,  /* the hybrid nodal-staggered cycle of Sec. 2 (the method) */
+  PIC_CYCLE_NODAL = 1    /* the nodal comparison cycle of Sec. 2: every quantity on the nodes,
+                            [k]_c in the solver, no centering */
+} pic_cycle;
+
 /*
  * Optional extension block (pass NULL for defaults).  struct_size must be
  * sizeof(pic_ext) of the caller's header (versioning).
@@ -90,6 +96,10 @@ typedef enum {
  *     rho^n and rho^{n+1} inside the step (the rho array keeps the unfiltered
  *     deposit; the J written back is the filtered, Yee-centered one).  Default 0.
  *   pusher: pic_pusher.  Default PIC_PUSHER_BORIS.
+ *   cycle: pic_cycle.  With PIC_CYCLE_NODAL the caller's E, B and the J written back
+ *     live on the nodes (no Yee offsets), the solver uses [k]_c in place of [k]_s (with
+ *     the Nyquist entry 0 at infinite order, the centered derivative of node-based data)
+ *     and zeta_F = 1.  Default PIC_CYCLE_HYBRID.
  *   reserved: must be 0.
  */
 typedef struct {
@@ -103,7 +113,8 @@ typedef struct {
   void* cuda_stream;
   int32_t filter_passes;
   int32_t pusher;
-  int32_t reserved[2];
+  int32_t cycle;
+  int32_t reserved;
 } pic_ext;
 
 /* Fill *ext with the defaults listed above. */
@@ -213,7 +224,7 @@ typedef struct {
  * The caller keeps checkpoints of the forward state and recomputes each step's
  * state before reversing it (pic_step must then run with sort_interval = 0 so
  * that particle order is stable).  PIC_ERR_UNSUPPORTED for the averaged variant,
- * the Vay pusher and filter_passes > 0.  Asynchronous.
+ * the Vay pusher, filter_passes > 0 and the nodal cycle.  Asynchronous.
  */
 pic_status pic_adjoint_step(pic_ctx* ctx, const double* const E[3], const double* const B[3],
                             const pic_species* sp, int n_species, double* const Ebar[3], double* const Bbar[3],
@@ -384,7 +395,8 @@ pic_status pic_stencil_extent(pic_ctx* ctx, const char* coef, int axis, double* 
  * doubles each in FFT order (k_j = 2 pi m_j / (N_a dx_a), m_j the signed index with the
  * Nyquist index at -N_a/2): ks = [k]_s and kc = [k]_c at the context's spectral order
  * (Sec. 4.1, Eqs. k_staggered / k_centered) and zeta = zeta_F, the Fourier symbol of the
- * centering of order centering_order[a] (App. C).  Any pointer may be NULL.  Synchronous.
+ * centering of order centering_order[a] (App. C).  Nodal cycle: ks = kc = the solver's
+ * [k]_c and zeta = 1.  Any pointer may be NULL.  Synchronous.
  */
 pic_status pic_axis_tables(pic_ctx* ctx, int axis, double* ks, double* kc, double* zeta);
 

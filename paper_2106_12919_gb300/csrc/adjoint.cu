@@ -259,8 +259,9 @@ extern "C" pic_status pic_adjoint_step(pic_ctx* ctx, const double* const E[3], c
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "the adjoint step is FP64 only");
   if (ctx->variant == PIC_PSATD_AVERAGED_GALILEAN)
     return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "no adjoint for the averaged Galilean variant");
-  if (ctx->filter_passes > 0 || ctx->pusher != PIC_PUSHER_BORIS)
-    return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "the adjoint covers the Boris pusher without smoothing");
+  if (ctx->filter_passes > 0 || ctx->pusher != PIC_PUSHER_BORIS || ctx->cycle != PIC_CYCLE_HYBRID)
+    return pic_set_error(ctx, PIC_ERR_UNSUPPORTED,
+                         "the adjoint covers the hybrid cycle with the Boris pusher and no smoothing");
   if (!nonnull(E, 3) || !nonnull(B, 3) || !nonnull(Ebar, 3) || !nonnull(Bbar, 3) || !rhobar)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   if (n_species < 0 || (n_species > 0 && (!sp || !spbar))) return pic_set_error(ctx, PIC_ERR_ARG, "species");

@@ -194,7 +194,8 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   if (!(e.c > 0.0) || !(e.eps0 > 0.0)) return fail(PIC_ERR_ARG, "c and eps0 must be > 0");
   if (e.filter_passes < 0 || e.filter_passes > 8) return fail(PIC_ERR_ARG, "filter_passes must be in [0, 8]");
   if (e.pusher != PIC_PUSHER_BORIS && e.pusher != PIC_PUSHER_VAY) return fail(PIC_ERR_ARG, "unknown pusher");
-  if (e.reserved[0] || e.reserved[1]) return fail(PIC_ERR_ARG, "reserved fields must be 0");
+  if (e.cycle != PIC_CYCLE_HYBRID && e.cycle != PIC_CYCLE_NODAL) return fail(PIC_ERR_ARG, "unknown cycle");
+  if (e.reserved) return fail(PIC_ERR_ARG, "reserved fields must be 0");
   if (psatd_variant != PIC_PSATD_STANDARD) {
     if (!v_gal) return fail(PIC_ERR_ARG, "v_gal required");
     const double v2 = v_gal[0] * v_gal[0] + v_gal[1] * v_gal[1] + v_gal[2] * v_gal[2];
@@ -217,6 +218,7 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   ctx->precision = e.precision;
   ctx->filter_passes = e.filter_passes;
   ctx->pusher = e.pusher;
+  ctx->cycle = e.cycle;
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) ctx->sp_off_n[q] = -1;
   ctx->stream = reinterpret_cast<cudaStream_t>(e.cuda_stream);
   ctx->ncell = grid[0] * grid[1] * grid[2];

@@ -86,6 +86,7 @@ struct pic_ctx {
   int precision;
   int filter_passes;  // bilinear smoothing passes of the deposits (0 = off)
   int pusher;         // pic_pusher
+  int cycle;          // pic_cycle
   cudaStream_t stream;
   int64_t ncell, nzh, nmode;
   int ncoef;

@@ -595,12 +595,22 @@ pic_status psatd_setup(pic_ctx* ctx) {
         sz += alpha_s(mc, n) * (long double)c;
       }
       zeta = (double)sz;
+      double s, c;
+      sincospi_frac(js, N, &s, &c);  // k dx / 2 = pi js / N
+      double2 shift = make_double2(c, -s);
+      if (ctx->cycle == PIC_CYCLE_NODAL) {
+        // nodal comparison cycle (Sec. 2): node-based fields, [k]_c in the solver (0 at the
+        // Nyquist index at infinite order: the centered derivative of node-based data), no
+        // centering and no half-cell offsets
+        if (ms == 0 && 2 * js == -N) kc = 0.0;
+        ks = kc;
+        zeta = 1.0;
+        shift = make_double2(1.0, 0.0);
+      }
       h[(0 + a) * Nmax + j] = ks;
       h[(3 + a) * Nmax + j] = kc;
       h[(6 + a) * Nmax + j] = zeta;
-      double s, c;
-      sincospi_frac(js, N, &s, &c);  // k dx / 2 = pi js / N
-      hs[a * Nmax + j] = make_double2(c, -s);
+      hs[a * Nmax + j] = shift;
     }
     ctx->cw[a].m = mc;
     for (int n = 1; n <= mc; ++n) ctx->cw[a].w[n - 1] = (double)(alpha_s(mc, n) / 2.0L);

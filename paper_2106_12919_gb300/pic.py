@@ -16,6 +16,7 @@ from . import build as _build
 PIC_OK = 0
 PIC_FP64, PIC_FP32 = 0, 1
 PIC_PUSHER_BORIS, PIC_PUSHER_VAY = 0, 1
+PIC_CYCLE_HYBRID, PIC_CYCLE_NODAL = 0, 1
 STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_UNSUPPORTED", -3: "PIC_ERR_NOMEM",
           -4: "PIC_ERR_CUDA", -5: "PIC_ERR_CAPACITY", -6: "PIC_ERR_TIMEOUT", -7: "PIC_ERR_NONFINITE"}
 STANDARD, GALILEAN, AVERAGED = 0, 1, 2
@@ -30,7 +31,7 @@ class PicExt(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("spectral_order", _i3), ("precision", ctypes.c_int32),
                 ("c", ctypes.c_double), ("eps0", ctypes.c_double), ("tile", _i3),
                 ("sort_interval", ctypes.c_int32), ("cuda_stream", _vp), ("filter_passes", ctypes.c_int32),
-                ("pusher", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("pusher", ctypes.c_int32), ("cycle", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PicSpecies(ctypes.Structure):
@@ -244,7 +245,7 @@ class Context:
     def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
                  v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0,
                  tile=(4, 8, 8), sort_interval=20, stream=None, precision=PIC_FP64, filter_passes=0,
-                 pusher=0):
+                 pusher=0, cycle=0):
         self.shape = tuple(int(n) for n in shape)
         self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
         self.nmode = self.shape[0] * self.shape[1] * (self.shape[2] // 2 + 1)
@@ -261,6 +262,7 @@ class Context:
         ext.precision = precision
         ext.filter_passes = filter_passes
         ext.pusher = pusher
+        ext.cycle = cycle
         self.precision = precision
         ext.cuda_stream = self.stream.cuda_stream
         h = _vp()

@@ -38,7 +38,7 @@ def test_ext_defaults():
     pic.LIB.pic_ext_default(ctypes.byref(e))
     assert e.struct_size == ctypes.sizeof(pic.PicExt)
     assert (e.c, e.eps0, list(e.tile), e.sort_interval) == (1.0, 1.0, [4, 8, 8], 20)
-    assert (e.filter_passes, e.pusher, list(e.reserved)) == (0, pic.PIC_PUSHER_BORIS, [0, 0])
+    assert (e.filter_passes, e.pusher, e.cycle, e.reserved) == (0, pic.PIC_PUSHER_BORIS, pic.PIC_CYCLE_HYBRID, 0)
 
 
 def test_init_rejects_bad_extension_fields():
@@ -46,19 +46,13 @@ def test_init_rejects_bad_extension_fields():
     from paper_2106_12919_gb300 import pic
     h = ctypes.c_void_p()
     L3, D3, I3 = ctypes.c_int64 * 3, ctypes.c_double * 3, ctypes.c_int32 * 3
-    for field, value in (("filter_passes", 9), ("filter_passes", -1), ("pusher", 2)):
+    for field, value in (("filter_passes", 9), ("filter_passes", -1), ("pusher", 2), ("cycle", 2), ("reserved", 1)):
         e = pic.PicExt()
         pic.LIB.pic_ext_default(ctypes.byref(e))
         setattr(e, field, value)
         st = pic.LIB.pic_init(ctypes.byref(h), L3(16, 16, 16), D3(1, 1, 1), 1.0, 1, I3(8, 8, 8), 0, D3(0, 0, 0),
                               ctypes.byref(e))
         assert st == -1 and not h.value, field
-    e = pic.PicExt()
-    pic.LIB.pic_ext_default(ctypes.byref(e))
-    e.reserved[1] = 3
-    st = pic.LIB.pic_init(ctypes.byref(h), L3(16, 16, 16), D3(1, 1, 1), 1.0, 1, I3(8, 8, 8), 0, D3(0, 0, 0),
-                          ctypes.byref(e))
-    assert st == -1 and not h.value
 
 
 def test_init_rejects_bad_arguments_without_gpu_work():

@@ -92,3 +92,21 @@ def test_beam_rms_fp64_and_fp32():
     # the FP32 positions / weights differ from the FP64 ones by rounding only
     assert abs(ref32 - ref) < 1e-6 * ref
     del torch
+
+
+def test_axis_tables_and_dispersion_of_the_nodal_cycle():
+    p = _params((16, 8, 32), (0.5, 1.0, 0.25), 0.2, (0, 8, 16), (0.0, 0.0, 0.0))
+    ctx = context_for(p, cycle=1)
+    kc = psatd.nodal_k(p["shape"], [fornberg.k_centered(p["shape"][a], p["dx"][a], p["spectral_order"][a])
+                                    for a in range(3)], p["spectral_order"])
+    for a in range(3):
+        ks, kcd, zt = (np.array(t) for t in ctx.axis_tables(a))
+        np.testing.assert_allclose(ks, np.asarray(kc[a], np.float64), rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(kcd, np.asarray(kc[a], np.float64), rtol=1e-14, atol=1e-14)
+        assert np.all(zt == 1.0)
+    co = psatd.coefficients(p["shape"], p["dx"], p["dt"], p["spectral_order"], nodal=True)
+    k = psatd.staggered_k_grid(p["shape"], p["dx"], p["spectral_order"], nodal=True)
+    for axis in range(3):
+        ref = diagnostics.vacuum_dispersion(co, k, axis, 1.0, p["dt"])
+        np.testing.assert_allclose(np.array(ctx.vacuum_dispersion(axis)), ref, rtol=1e-12,
+                                   atol=1e-12 * np.max(np.abs(ref)))

@@ -155,6 +155,8 @@ CASES = [
     # Vay's pusher
     ("laser_wakefield:vay", dict(shape=(16, 16, 64), ppc=1), 100, False),
     ("beam_wakefield:vay", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 100, False),
+    # the nodal comparison cycle
+    ("laser_wakefield:nodal", dict(shape=(16, 16, 64), ppc=1), 100, False),
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 100, True),
     ("galilean_drift", dict(shape=(16, 16, 32), ppc=1), 100, True),
 ]
@@ -192,6 +194,8 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
     opts = {"filter_passes": int(opt[len("filter"):])} if opt.startswith("filter") else {}
     if opt == "vay":
         opts = {"pusher": 1}
+    if opt == "nodal":
+        opts = {"cycle": 1}
     w = workloads.WORKLOADS[name](**kw)
     p = w["params"]
     shape, dx = p["shape"], p["dx"]

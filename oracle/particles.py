@@ -28,9 +28,10 @@ x^{n+1/2} = x^n + dt (v - v_gal) / 2, and rho^{n+1} = sum_p q w S(x^{n+1} - x_i)
 import numpy as np
 
 
-def shape_weights(x, inv_dx, order):
-    """(lowest node index, weights[order+1, N]) of the order-`order` B-spline at positions x."""
-    t = x * inv_dx
+def shape_weights(x, inv_dx, order, offset=0.0):
+    """(lowest node index, weights[order+1, N]) of the order-`order` B-spline at positions x,
+    for a grid whose node i sits at (i + offset) dx (offset 1/2: a staggered Yee axis)."""
+    t = x * inv_dx - offset
     if order == 2:
         base = np.floor(t + 0.5)
     else:
@@ -49,11 +50,12 @@ def shape_weights(x, inv_dx, order):
     raise ValueError("shape order must be 1, 2 or 3")
 
 
-def _node_loop(pos, shape, dx, order):
-    """Yield (ix, iy, iz, S) for every one of the (order+1)^3 nodes around each particle."""
+def _node_loop(pos, shape, dx, order, offset=(0.0, 0.0, 0.0)):
+    """Yield (ix, iy, iz, S) for every one of the (order+1)^3 nodes around each particle
+    (grid points at (i + offset_a) dx_a)."""
     lo, w = [], []
     for a in range(3):
-        l, ww = shape_weights(pos[a], 1.0 / dx[a], order)
+        l, ww = shape_weights(pos[a], 1.0 / dx[a], order, offset[a])
         lo.append(l)
         w.append(ww)
     for i in range(order + 1):
@@ -66,24 +68,26 @@ def _node_loop(pos, shape, dx, order):
                 yield ix, iy, iz, sxy * w[2][k]
 
 
-def gather(fields, pos, dx, order):
-    """Interpolate nodal fields (list of (Nx,Ny,Nz) arrays) to particle positions.
+def gather(fields, pos, dx, order, offset=(0.0, 0.0, 0.0)):
+    """Interpolate fields (list of (Nx,Ny,Nz) arrays on the same grid, points at
+    (i + offset) dx; nodal by default) to particle positions.
 
     F(x_p) = sum_{ijk} S(x_p - x_i) S(y_p - y_j) S(z_p - z_k) F_{ijk}  (gather step of Sec. 2).
     """
     shape = fields[0].shape
     out = [np.zeros_like(pos[0]) for _ in fields]
-    for ix, iy, iz, S in _node_loop(pos, shape, dx, order):
+    for ix, iy, iz, S in _node_loop(pos, shape, dx, order, offset):
         for f, o in zip(fields, out):
             o += S * f[ix, iy, iz]
     return out
 
 
-def deposit(grid_shape, pos, values, dx, order):
-    """Scatter per-particle values onto nodal arrays: rho_i = sum_p v_p S(x_p - x_i) / dV."""
+def deposit(grid_shape, pos, values, dx, order, offset=(0.0, 0.0, 0.0)):
+    """Scatter per-particle values onto arrays with points at (i + offset) dx (nodal by
+    default): rho_i = sum_p v_p S(x_p - x_i) / dV."""
     dV = dx[0] * dx[1] * dx[2]
     out = [np.zeros(grid_shape) for _ in values]
-    for ix, iy, iz, S in _node_loop(pos, grid_shape, dx, order):
+    for ix, iy, iz, S in _node_loop(pos, grid_shape, dx, order, offset):
         for v, o in zip(values, out):
             np.add.at(o, (ix, iy, iz), v * S)
     return [o / dV for o in out]
@@ -140,25 +144,39 @@ def wrap(x, L):
     return np.where(x < 0.0, x + L, x)
 
 
+# Yee offsets (in cells) of E, B and J components, for the staggered comparison cycle
+_YEE_E = ((0.5, 0.0, 0.0), (0.0, 0.5, 0.0), (0.0, 0.0, 0.5))
+_YEE_B = ((0.0, 0.5, 0.5), (0.5, 0.0, 0.5), (0.5, 0.5, 0.0))
+
+
 def push_and_deposit(sp, nodal_E, nodal_B, grid_shape, dx, dt, order, v_gal=(0.0, 0.0, 0.0), c=1.0,
-                     pusher=0):
+                     pusher=0, staggered=False):
     """Gather at x^n, push (Boris, or Vay with pusher = 1), move, and deposit J^{n+1/2} and
     rho^{n+1} for one species.
 
     sp: dict with x, y, z, ux, uy, uz, w (float64 arrays) and q, m (floats).
-    Returns (new species dict, [Jx, Jy, Jz] nodal, rho nodal).
+    staggered: the staggered comparison cycle of Sec. 2: E, B are gathered from their own Yee
+    positions and J is deposited at its Yee positions (rho stays nodal).
+    Returns (new species dict, [Jx, Jy, Jz] nodal (Yee if staggered), rho nodal).
     """
     L = [grid_shape[a] * dx[a] for a in range(3)]
     pos = [sp["x"], sp["y"], sp["z"]]
-    E = gather(nodal_E, pos, dx, order)
-    B = gather(nodal_B, pos, dx, order)
+    if staggered:
+        E = [gather([nodal_E[a]], pos, dx, order, _YEE_E[a])[0] for a in range(3)]
+        B = [gather([nodal_B[a]], pos, dx, order, _YEE_B[a])[0] for a in range(3)]
+    else:
+        E = gather(nodal_E, pos, dx, order)
+        B = gather(nodal_B, pos, dx, order)
     u = PUSHERS[pusher]([sp["ux"], sp["uy"], sp["uz"]], E, B, sp["q"], sp["m"], dt, c)
     g = np.sqrt(1.0 + (u[0] ** 2 + u[1] ** 2 + u[2] ** 2) / (c * c))
     v = [u[a] / g for a in range(3)]
     mid = [wrap(pos[a] + 0.5 * dt * (v[a] - v_gal[a]), L[a]) for a in range(3)]
     new = [wrap(pos[a] + dt * (v[a] - v_gal[a]), L[a]) for a in range(3)]
     qw = sp["q"] * sp["w"]
-    J = deposit(grid_shape, mid, [qw * v[0], qw * v[1], qw * v[2]], dx, order)
+    if staggered:
+        J = [deposit(grid_shape, mid, [qw * v[a]], dx, order, _YEE_E[a])[0] for a in range(3)]
+    else:
+        J = deposit(grid_shape, mid, [qw * v[0], qw * v[1], qw * v[2]], dx, order)
     (rho,) = deposit(grid_shape, new, [qw], dx, order)
     out = dict(sp)
     out.update(x=new[0], y=new[1], z=new[2], ux=u[0], uy=u[1], uz=u[2])

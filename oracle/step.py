@@ -10,8 +10,10 @@ One step, in the paper's order:
   5. solve Maxwell's equations on the Yee grid in Fourier space (Sec. 4): forward
      transforms, PSATD update, inverse transforms.
 
-Nodal comparison cycle (Sec. 2, the "standard" PSATD PIC cycle on a nodal grid): every
-quantity on the nodes, the centered modified wave numbers [k]_c in the solver, no centering.
+Comparison cycles (Sec. 2, the "standard" PSATD PIC cycle): NODAL: every quantity on the
+nodes, the centered modified wave numbers [k]_c in the solver, no centering; STAGGERED: the
+Yee-grid solver of the hybrid cycle, with E, B gathered from and J deposited at their own Yee
+positions (rho nodal), no centering.
 
 Averaged Galilean variant (Sec. 4.4): the Yee state E, B evolves with the
 Galilean update; the averaged fields <E>^{n+1}, <B>^{n+1} computed alongside are
@@ -23,7 +25,7 @@ import numpy as np
 from . import grid, particles, psatd
 
 STANDARD, GALILEAN, AVERAGED = 0, 1, 2
-HYBRID, NODAL = 0, 1
+HYBRID, NODAL, STAGGERED = 0, 1, 2
 
 
 class Params:
@@ -44,7 +46,7 @@ class Params:
         self.eps0 = float(eps0)
         self.filter_passes = int(filter_passes)
         self.pusher = int(pusher)        # 0: Boris, 1: Vay
-        self.cycle = int(cycle)          # HYBRID (Sec. 2) or the fully NODAL comparison cycle
+        self.cycle = int(cycle)          # HYBRID (Sec. 2), or the NODAL or STAGGERED comparison cycle
         self._co = None
         self._k = None
 
@@ -65,9 +67,9 @@ def maxwell_update(p, E, B, J, rho_n, rho_np1):
     """
     co, k = p.coefficients()
     # positions of the components: the Yee grid, or the nodes in the nodal cycle
-    nE = grid.E_NAMES if p.cycle == HYBRID else ("rho",) * 3
-    nB = grid.B_NAMES if p.cycle == HYBRID else ("rho",) * 3
-    nJ = grid.J_NAMES if p.cycle == HYBRID else ("rho",) * 3
+    nE = ("rho",) * 3 if p.cycle == NODAL else grid.E_NAMES
+    nB = ("rho",) * 3 if p.cycle == NODAL else grid.B_NAMES
+    nJ = ("rho",) * 3 if p.cycle == NODAL else grid.J_NAMES
     Eh = [grid.to_spectral(E[a], nE[a], p.dx) for a in range(3)]
     Bh = [grid.to_spectral(B[a], nB[a], p.dx) for a in range(3)]
     Jh = [grid.to_spectral(J[a], nJ[a], p.dx) for a in range(3)]
@@ -101,7 +103,7 @@ def hybrid_step(p, state):
     if p.variant == AVERAGED and state.get("avg") is not None:
         gE, gB = state["avg"]
     o = p.centering_order
-    if p.cycle == NODAL:          # nodal comparison cycle: E, B already live on the nodes
+    if p.cycle in (NODAL, STAGGERED):   # comparison cycles: gather E, B where they live
         nE, nB = [np.asarray(f) for f in gE], [np.asarray(f) for f in gB]
     else:
         nE = [grid.center_to_nodal(gE[a], grid.E_NAMES[a], o) for a in range(3)]      # step 1
@@ -111,7 +113,7 @@ def hybrid_step(p, state):
     new_species = []
     for sp in state["species"]:                                                       # steps 2-3
         nsp, J, r = particles.push_and_deposit(sp, nE, nB, p.shape, p.dx, p.dt, p.shape_order,
-                                               p.v_gal, p.c, p.pusher)
+                                               p.v_gal, p.c, p.pusher, staggered=p.cycle == STAGGERED)
         new_species.append(nsp)
         for a in range(3):
             Jn[a] += J[a]
@@ -122,7 +124,7 @@ def hybrid_step(p, state):
     Jf = [grid.bilinear_filter(Jn[a], f) for a in range(3)] if f else Jn
     rn_f = grid.bilinear_filter(state["rho"], f) if f else state["rho"]
     rp_f = grid.bilinear_filter(rho_np1, f) if f else rho_np1
-    if p.cycle == NODAL:
+    if p.cycle in (NODAL, STAGGERED):   # J already lives where the solver needs it
         Jy = Jf
     else:
         Jy = [grid.center_to_yee(Jf[a], grid.J_NAMES[a], o) for a in range(3)]         # step 4

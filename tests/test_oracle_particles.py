@@ -142,3 +142,25 @@ def test_vay_pure_electric_kick():
     un = particles.vay(u, E, Z, 2.0, 0.5, 0.1, 1.0)
     for a in range(3):
         np.testing.assert_allclose(un[a], u[a] + 2.0 / 0.5 * 0.1 * E[a], rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_offset_grid_gather_is_exact_for_linear_fields_and_deposit_keeps_moments(order):
+    # grid points at (i + 1/2) dx along x (a Yee axis): a field linear in x sampled there is
+    # gathered exactly, and deposits keep the charge and the first moment
+    from oracle import particles
+    shape, dx = (16, 8, 8), (0.5, 1.0, 2.0)
+    rng = np.random.default_rng(order)
+    n = 64
+    pos = [rng.uniform(2.0, 6.0, n), rng.uniform(0, 8.0, n), rng.uniform(4.0, 12.0, n)]
+    off = (0.5, 0.0, 0.5)
+    X = [(np.arange(shape[a]) + off[a]) * dx[a] for a in range(3)]
+    Xg = np.meshgrid(*X, indexing="ij")
+    F = 1.5 + 0.25 * Xg[0] - 0.125 * Xg[2]
+    (g,) = particles.gather([F], pos, dx, order, off)
+    np.testing.assert_allclose(g, 1.5 + 0.25 * pos[0] - 0.125 * pos[2], rtol=1e-13, atol=1e-13)
+    w = rng.uniform(0.5, 1.5, n)
+    (d,) = particles.deposit(shape, pos, [w], dx, order, off)
+    dV = np.prod(dx)
+    assert abs(d.sum() * dV - w.sum()) < 1e-12 * w.sum()
+    assert abs((d * Xg[0]).sum() * dV - (w * pos[0]).sum()) < 1e-11 * (w * pos[0]).sum()

@@ -149,3 +149,17 @@ def test_nodal_cycle_charge_conserved():
         step.hybrid_step(p, st)
         assert abs(np.sum(st["rho"]) * np.prod(p.dx) - qtot) < 1e-12 * qabs
         assert st["max_imag"] < 1e-9 * max(1.0, max(np.abs(e).max() for e in st["E"]))
+
+
+def test_staggered_cycle_charge_conserved_and_real():
+    w = workloads.laser_wakefield(shape=(8, 8, 32), ppc=1)
+    p = step.Params(**w["params"], cycle=step.STAGGERED)
+    st = {"E": [a.copy() for a in w["E"]], "B": [a.copy() for a in w["B"]],
+          "species": [dict(s) for s in w["species"]]}
+    st["rho"] = step.initial_rho(p, st["species"])
+    qtot = sum(float(np.sum(s["q"] * s["w"])) for s in st["species"])
+    qabs = sum(float(np.sum(np.abs(s["q"] * s["w"]))) for s in st["species"])
+    for _ in range(3):
+        step.hybrid_step(p, st)
+        assert abs(np.sum(st["rho"]) * np.prod(p.dx) - qtot) < 1e-12 * qabs
+        assert st["max_imag"] < 1e-9 * max(1.0, max(np.abs(e).max() for e in st["E"]))

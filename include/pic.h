@@ -74,8 +74,10 @@ typedef enum {
 
 typedef enum {
   PIC_CYCLE_HYBRID = 0,  /* the hybrid nodal-staggered cycle of Sec. 2 (the method) */
-  PIC_CYCLE_NODAL = 1    /* the nodal comparison cycle of Sec. 2: every quantity on the nodes,
+  PIC_CYCLE_NODAL = 1,   /* the nodal comparison cycle of Sec. 2: every quantity on the nodes,
                             [k]_c in the solver, no centering */
+  PIC_CYCLE_STAGGERED = 2  /* the staggered comparison cycle of Sec. 2: the Yee-grid solver, E, B
+                              gathered from and J deposited at their own Yee positions, no centering */
 } pic_cycle;
 
 /*
@@ -99,7 +101,10 @@ typedef enum {
  *   cycle: pic_cycle.  With PIC_CYCLE_NODAL the caller's E, B and the J written back
  *     live on the nodes (no Yee offsets), the solver uses [k]_c in place of [k]_s (with
  *     the Nyquist entry 0 at infinite order, the centered derivative of node-based data)
- *     and zeta_F = 1.  Default PIC_CYCLE_HYBRID.
+ *     and zeta_F = 1.  With PIC_CYCLE_STAGGERED the fields stay on the Yee grid throughout:
+ *     the shapes of each component are taken on its own staggered grid (offset 1/2 cell
+ *     along its staggered axes) for the gather of E, B and the deposit of J (rho nodal), and
+ *     zeta_F = 1.  The FP32 form then uses the untiled push.  Default PIC_CYCLE_HYBRID.
  *   reserved: must be 0.
  */
 typedef struct {
@@ -396,7 +401,7 @@ pic_status pic_stencil_extent(pic_ctx* ctx, const char* coef, int axis, double* 
  * Nyquist index at -N_a/2): ks = [k]_s and kc = [k]_c at the context's spectral order
  * (Sec. 4.1, Eqs. k_staggered / k_centered) and zeta = zeta_F, the Fourier symbol of the
  * centering of order centering_order[a] (App. C).  Nodal cycle: ks = kc = the solver's
- * [k]_c and zeta = 1.  Any pointer may be NULL.  Synchronous.
+ * [k]_c and zeta = 1; staggered cycle: zeta = 1.  Any pointer may be NULL.  Synchronous.
  */
 pic_status pic_axis_tables(pic_ctx* ctx, int axis, double* ks, double* kc, double* zeta);
 

@@ -194,7 +194,7 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   if (!(e.c > 0.0) || !(e.eps0 > 0.0)) return fail(PIC_ERR_ARG, "c and eps0 must be > 0");
   if (e.filter_passes < 0 || e.filter_passes > 8) return fail(PIC_ERR_ARG, "filter_passes must be in [0, 8]");
   if (e.pusher != PIC_PUSHER_BORIS && e.pusher != PIC_PUSHER_VAY) return fail(PIC_ERR_ARG, "unknown pusher");
-  if (e.cycle != PIC_CYCLE_HYBRID && e.cycle != PIC_CYCLE_NODAL) return fail(PIC_ERR_ARG, "unknown cycle");
+  if (e.cycle < PIC_CYCLE_HYBRID || e.cycle > PIC_CYCLE_STAGGERED) return fail(PIC_ERR_ARG, "unknown cycle");
   if (e.reserved) return fail(PIC_ERR_ARG, "reserved fields must be 0");
   if (psatd_variant != PIC_PSATD_STANDARD) {
     if (!v_gal) return fail(PIC_ERR_ARG, "v_gal required");
@@ -359,7 +359,7 @@ pic_status pic_maxwell_step(pic_ctx* ctx, double* const E[3], double* const B[3]
   rout.p[0] = ctx->rhoh[0];
   rout.p[1] = ctx->rhoh[1];
   PIC_TRY(fft_r2c(ctx, rin, rout, 2));
-  PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[0], ctx->rhoh[1], 1, 1, 0));
+  PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[0], ctx->rhoh[1], 1, 1, 0, 0));
   if (avg) {
     RPtr6 o;
     CPtr6 gg;
@@ -432,11 +432,20 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
     StageScope t(ctx, STAGE_FFT, 3);
     PIC_TRY(fft_r2c(ctx, rin, rout, 1));
   }
-  {
-    StageScope t(ctx, STAGE_OTHER, 1);
-    PIC_TRY(psatd_to_nodal(ctx, ctx->EBh, 1.0 / (double)nc));
+  const bool stag = ctx->cycle == PIC_CYCLE_STAGGERED;
+  if (stag) {
+    // staggered comparison cycle: the first gather reads the caller's Yee E, B as they are
+    const double* src[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
+    for (int c = 0; c < 6; ++c)
+      PIC_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->nodal + c * nc, src[c], nc * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        ctx->stream));
+  } else {
+    {
+      StageScope t(ctx, STAGE_OTHER, 1);
+      PIC_TRY(psatd_to_nodal(ctx, ctx->EBh, 1.0 / (double)nc));
+    }
+    PIC_TRY(g_to_nodal(ctx));
   }
-  PIC_TRY(g_to_nodal(ctx));
   const double* En[3] = {ctx->nodal, ctx->nodal + nc, ctx->nodal + 2 * nc};
   const double* Bn[3] = {ctx->nodal + 3 * nc, ctx->nodal + 4 * nc, ctx->nodal + 5 * nc};
   double* Jn[3] = {ctx->Jn, ctx->Jn + nc, ctx->Jn + 2 * nc};
@@ -465,9 +474,18 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
       StageScope t(ctx, STAGE_FFT, 3);
       PIC_TRY(fft_r2c(ctx, in, out, 4));
     }
+    if (stag) {
+      // J was deposited at its Yee positions: plain DFT -> paper convention, in place
+      CPtr6 jh;
+      for (int c = 0; c < 3; ++c) jh.p[c] = ctx->Jh + c * nm;
+      StageScope t(ctx, STAGE_OTHER, 1);
+      PIC_TRY(psatd_phase(ctx, jh, jh, kKindJ, 3, -1, 1.0));
+    }
     {
+      // hybrid: J nodal (centered in the update), G = nodal E, B; staggered: J and G on the Yee grid
       StageScope t(ctx, STAGE_UPDATE, 1);
-      PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], 0, 0, last ? 1 : 0));
+      PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], stag ? 1 : 0, stag ? 1 : 0, last ? 1 : 0,
+                              1));
     }
     cur = 1 - cur;
     if (!last) PIC_TRY(g_to_nodal(ctx));

@@ -201,17 +201,26 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     StageScope t(ctx, STAGE_FFT, 3);
     PIC_TRY32(fft_r2c<float>(ctx, rin, rout, 1));
   }
-  {
-    StageScope t(ctx, STAGE_OTHER, 1);
-    PIC_TRY32(psatd_to_nodal32(ctx, EBh(ctx), Gs(ctx), 1.0 / (double)nc));
+  const bool stag = ctx->cycle == PIC_CYCLE_STAGGERED;
+  if (stag) {
+    // staggered comparison cycle: the first gather reads the caller's Yee E, B as they are
+    const float* src[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
+    for (int c = 0; c < 6; ++c)
+      PIC_CUDA_TRY(ctx, cudaMemcpyAsync(nodal(ctx) + c * nc, src[c], nc * sizeof(float), cudaMemcpyDeviceToDevice,
+                                        ctx->stream));
+  } else {
+    {
+      StageScope t(ctx, STAGE_OTHER, 1);
+      PIC_TRY32(psatd_to_nodal32(ctx, EBh(ctx), Gs(ctx), 1.0 / (double)nc));
+    }
+    PIC_TRY32(g_to_nodal32(ctx));
   }
-  PIC_TRY32(g_to_nodal32(ctx));
   float* nd = nodal(ctx);
   const float* En[3] = {nd, nd + nc, nd + 2 * nc};
   const float* Bn[3] = {nd + 3 * nc, nd + 4 * nc, nd + 5 * nc};
   float* jn = Jn(ctx);
   float* Jnp[3] = {jn, jn + nc, jn + 2 * nc};
-  const bool tiled = ctx->sort_interval > 0 && tiled_push_fits(ctx);
+  const bool tiled = ctx->sort_interval > 0 && tiled_push_fits(ctx) && !stag;
   int64_t total = 0;
   for (int q = 0; q < n_species; ++q) total += sp[q].n;
   if (tiled && !ctx->bin_gate) {
@@ -266,10 +275,18 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
       StageScope t(ctx, STAGE_FFT, 3);
       PIC_TRY32(fft_r2c<float>(ctx, in, out, 4));
     }
+    if (stag) {
+      // J was deposited at its Yee positions: plain DFT -> paper convention, in place
+      CP6<float2> jh;
+      for (int c = 0; c < 3; ++c) jh.p[c] = Jh(ctx) + c * nm;
+      StageScope t(ctx, STAGE_OTHER, 1);
+      PIC_TRY32(psatd_phase32(ctx, jh, jh, kKindJ, 3, -1, 1.0));
+    }
     {
+      // hybrid: J nodal (centered in the update), G = nodal E, B; staggered: J and G on the Yee grid
       StageScope t(ctx, STAGE_UPDATE, 1);
-      PIC_TRY32(psatd_update32(ctx, EBh(ctx), Jh(ctx), rhoh(ctx, cur), rhoh(ctx, 1 - cur), Gs(ctx), 0, 0,
-                               last ? 1 : 0));
+      PIC_TRY32(psatd_update32(ctx, EBh(ctx), Jh(ctx), rhoh(ctx, cur), rhoh(ctx, 1 - cur), Gs(ctx), stag ? 1 : 0,
+                               stag ? 1 : 0, last ? 1 : 0, 1));
     }
     cur = 1 - cur;
     if (!last) PIC_TRY32(g_to_nodal32(ctx));

@@ -34,9 +34,11 @@ struct PushArgs {
   int vay;             // 1: Vay's pusher instead of Boris
 };
 
+// shape of order P at position x on a grid whose points sit at (i + off) dx (off = 0: nodes,
+// off = 1/2: a staggered Yee axis): t = x / dx - off
 template <int P>
-__device__ __forceinline__ void shape(double x, double inv, int mask, int& lo, double* S) {
-  const double t = __dmul_rn(x, inv);
+__device__ __forceinline__ void shape(double x, double inv, int mask, int& lo, double* S, double off = 0.0) {
+  const double t = __dmul_rn(x, inv) - off;
   double base;
   if (P == 2) base = floor(__dadd_rn(t, 0.5));
   else base = floor(t);
@@ -61,6 +63,30 @@ __device__ __forceinline__ void shape(double x, double inv, int mask, int& lo, d
     S[3] = d3 * (1.0 / 6.0);
   }
   (void)mask;
+}
+
+// u^{n-1/2} of particle p -> u^{n+1/2} with the gathered f = (E, B): Boris rotation, or Vay's pusher
+__device__ __forceinline__ void push_u(const PushArgs& a, int64_t p, const double* f, double& ux, double& uy,
+                                       double& uz) {
+  const double k = a.qm_half_dt;
+  if (a.vay) {
+    ux = a.ux[p];
+    uy = a.uy[p];
+    uz = a.uz[p];
+    vay_push<double>(ux, uy, uz, f, k, a.inv_c2);
+    return;
+  }
+  const double umx = a.ux[p] + k * f[0], umy = a.uy[p] + k * f[1], umz = a.uz[p] + k * f[2];
+  const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
+  const double tx = k * f[3] / gm, ty = k * f[4] / gm, tz = k * f[5] / gm;
+  const double s2 = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
+  const double sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+  const double upx = umx + (umy * tz - umz * ty);
+  const double upy = umy + (umz * tx - umx * tz);
+  const double upz = umz + (umx * ty - umy * tx);
+  ux = umx + (upy * sz - upz * sy) + k * f[0];
+  uy = umy + (upz * sx - upx * sz) + k * f[1];
+  uz = umz + (upx * sy - upy * sx) + k * f[2];
 }
 
 __device__ __forceinline__ double wrap(double x, double L) {
@@ -117,26 +143,8 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
     }
   }
   // push u^{n-1/2} -> u^{n+1/2}
-  const double k = a.qm_half_dt;
   double ux, uy, uz;
-  if (a.vay) {
-    ux = a.ux[p];
-    uy = a.uy[p];
-    uz = a.uz[p];
-    vay_push<double>(ux, uy, uz, f, k, a.inv_c2);
-  } else {  // Boris
-    const double umx = a.ux[p] + k * f[0], umy = a.uy[p] + k * f[1], umz = a.uz[p] + k * f[2];
-    const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
-    const double tx = k * f[3] / gm, ty = k * f[4] / gm, tz = k * f[5] / gm;
-    const double s2 = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
-    const double sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
-    const double upx = umx + (umy * tz - umz * ty);
-    const double upy = umy + (umz * tx - umx * tz);
-    const double upz = umz + (umx * ty - umy * tx);
-    ux = umx + (upy * sz - upz * sy) + k * f[0];
-    uy = umy + (upz * sx - upx * sz) + k * f[1];
-    uz = umz + (upx * sy - upy * sx) + k * f[2];
-  }
+  push_u(a, p, f, ux, uy, uz);
   const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
   const double vx = ux * ig, vy = uy * ig, vz = uz * ig;
   // move: x^{n+1} = x^n + dt (v - v_gal); J at x^{n+1/2}
@@ -188,6 +196,103 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
   }
 }
 
+// Staggered comparison cycle (Sec. 2): E, B are gathered from their own Yee positions and J is
+// deposited at its Yee positions (rho stays nodal).  Component c is staggered along the axes of
+// its bit mask (E: x, y, z; B: yz, xz, xy); shapes on the staggered axes use offset 1/2.
+template <int P>
+__device__ __forceinline__ double gather_one(const double* F, const PushArgs& a, const int* lo, const double* Sx,
+                                             const double* Sy, const double* Sz) {
+  constexpr int NS = P + 1;
+  double v = 0.0;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const int64_t ox = (int64_t)((lo[0] + i) & a.mask[0]) * a.Ny;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const int64_t oy = (ox + ((lo[1] + j) & a.mask[1])) * a.Nz;
+      const double sxy = Sx[i] * Sy[j];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) v += sxy * Sz[k] * __ldg(F + oy + ((lo[2] + k) & a.mask[2]));
+    }
+  }
+  return v;
+}
+
+template <int P>
+__device__ __forceinline__ void deposit_one(double* F, const PushArgs& a, const int* lo, const double* Sx,
+                                            const double* Sy, const double* Sz, double val) {
+  constexpr int NS = P + 1;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const int64_t ox = (int64_t)((lo[0] + i) & a.mask[0]) * a.Ny;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const int64_t oy = (ox + ((lo[1] + j) & a.mask[1])) * a.Nz;
+      const double sxy = Sx[i] * Sy[j] * val;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) atomicAdd(F + oy + ((lo[2] + k) & a.mask[2]), sxy * Sz[k]);
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) push_stag_kernel(PushArgs a) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= a.n) return;
+  constexpr int NS = P + 1;
+  const double x[3] = {a.x[p], a.y[p], a.z[p]};
+  const double qw = a.w[p] * a.qw_scale;
+  // shapes on the nodal (0) and staggered (1) grid of every axis
+  int l0[3], l1[3];
+  double S0[3][NS], S1[3][NS];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    shape<P>(x[d], a.inv_dx[d], a.mask[d], l0[d], S0[d], 0.0);
+    shape<P>(x[d], a.inv_dx[d], a.mask[d], l1[d], S1[d], 0.5);
+  }
+  constexpr int kStag[6] = {1, 2, 4, 6, 5, 3};  // Ex, Ey, Ez, Bx, By, Bz
+  double f[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int m = kStag[c];
+    const int lo[3] = {(m & 1) ? l1[0] : l0[0], (m & 2) ? l1[1] : l0[1], (m & 4) ? l1[2] : l0[2]};
+    f[c] = gather_one<P>(a.F[c], a, lo, (m & 1) ? S1[0] : S0[0], (m & 2) ? S1[1] : S0[1], (m & 4) ? S1[2] : S0[2]);
+  }
+  double ux, uy, uz;
+  push_u(a, p, f, ux, uy, uz);
+  const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
+  const double v[3] = {ux * ig, uy * ig, uz * ig};
+  double mid[3], nw[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double dd = a.dt * (v[d] - a.vg[d]);
+    mid[d] = wrap(x[d] + 0.5 * dd, a.L[d]);
+    nw[d] = wrap(x[d] + dd, a.L[d]);
+  }
+  a.x[p] = nw[0];
+  a.y[p] = nw[1];
+  a.z[p] = nw[2];
+  a.ux[p] = ux;
+  a.uy[p] = uy;
+  a.uz[p] = uz;
+  // J^{n+1/2}: component d at its Yee positions (staggered along axis d)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    shape<P>(mid[d], a.inv_dx[d], a.mask[d], l0[d], S0[d], 0.0);
+    shape<P>(mid[d], a.inv_dx[d], a.mask[d], l1[d], S1[d], 0.5);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lo[3] = {c == 0 ? l1[0] : l0[0], c == 1 ? l1[1] : l0[1], c == 2 ? l1[2] : l0[2]};
+    deposit_one<P>(a.J[c], a, lo, c == 0 ? S1[0] : S0[0], c == 1 ? S1[1] : S0[1], c == 2 ? S1[2] : S0[2],
+                   qw * v[c]);
+  }
+  // rho^{n+1} on the nodes
+#pragma unroll
+  for (int d = 0; d < 3; ++d) shape<P>(nw[d], a.inv_dx[d], a.mask[d], l0[d], S0[d], 0.0);
+  deposit_one<P>(a.rho, a, l0, S0[0], S0[1], S0[2], qw);
+}
+
 PushArgs make_args(pic_ctx* ctx, const pic_species* sp) {
   PushArgs a;
   a.x = sp->x;
@@ -218,6 +323,15 @@ pic_status launch_push(pic_ctx* ctx, const PushArgs& a) {
   if (a.n == 0) return PIC_OK;
   const int bs = 256;
   const unsigned nb = (unsigned)((a.n + bs - 1) / bs);
+  if (a.gather && ctx->cycle == PIC_CYCLE_STAGGERED) {
+    switch (ctx->shape_order) {
+      case 1: push_stag_kernel<1><<<nb, bs, 0, ctx->stream>>>(a); break;
+      case 2: push_stag_kernel<2><<<nb, bs, 0, ctx->stream>>>(a); break;
+      default: push_stag_kernel<3><<<nb, bs, 0, ctx->stream>>>(a); break;
+    }
+    PIC_LAUNCH_CHECK(ctx);
+    return PIC_OK;
+  }
   switch (ctx->shape_order) {
     case 1: push_kernel<1><<<nb, bs, 0, ctx->stream>>>(a); break;
     case 2: push_kernel<2><<<nb, bs, 0, ctx->stream>>>(a); break;

@@ -267,6 +267,123 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
   deposit_node_block<P>(a, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
 }
 
+// Staggered comparison cycle (Sec. 2), FP32 form: E, B gathered from their own Yee positions,
+// J deposited at its Yee positions, rho on the nodes; untiled, global atomics.  On an axis
+// staggered by half a cell the shape is taken for (cell, offset) shifted by -1/2:
+// offset f >= 1/2 -> (i, f - 1/2), else (i - 1, f + 1/2).
+__device__ __forceinline__ void half_shift_cell(int i, float f, int& is, float& fs) {
+  if (f >= 0.5f) {
+    is = i;
+    fs = f - 0.5f;
+  } else {
+    is = i - 1;
+    fs = f + 0.5f;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ float gather32_one(const float* F, const Push32Args& a, const int* lo, const float* Sx,
+                                              const float* Sy, const float* Sz) {
+  constexpr int NS = P + 1;
+  float v = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const int64_t ox = (int64_t)((lo[0] + i) & a.mask[0]) * a.Ny;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const int64_t oy = (ox + ((lo[1] + j) & a.mask[1])) * a.Nz;
+      const float sxy = Sx[i] * Sy[j];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) v += sxy * Sz[k] * __ldg(F + oy + ((lo[2] + k) & a.mask[2]));
+    }
+  }
+  return v;
+}
+
+template <int P>
+__device__ __forceinline__ void deposit32_one(float* F, const Push32Args& a, const int* lo, const float* Sx,
+                                              const float* Sy, const float* Sz, float val) {
+  constexpr int NS = P + 1;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const int64_t ox = (int64_t)((lo[0] + i) & a.mask[0]) * a.Ny;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const int64_t oy = (ox + ((lo[1] + j) & a.mask[1])) * a.Nz;
+      const float sxy = Sx[i] * Sy[j] * val;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) atomicAdd(F + oy + ((lo[2] + k) & a.mask[2]), sxy * Sz[k]);
+    }
+  }
+}
+
+// shapes of (cell c[d], offset f[d]) on the nodal (0) and staggered (1) grid of every axis
+template <int P>
+__device__ __forceinline__ void shapes_both(const int* c, const float* f, int* l0, int* l1, float (*S0)[P + 1],
+                                            float (*S1)[P + 1]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    shape32<P>(c[d], f[d], l0[d], S0[d]);
+    int is;
+    float fs;
+    half_shift_cell(c[d], f[d], is, fs);
+    shape32<P>(is, fs, l1[d], S1[d]);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) push32_stag_kernel(Push32Args a) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= a.n) return;
+  constexpr int NS = P + 1;
+  const int cl = a.cell[p];
+  const int ci[3] = {(cl >> (a.shz + a.shy)) & a.mask[0], (cl >> a.shz) & a.mask[1], cl & a.mask[2]};
+  const float fo[3] = {a.fx[p], a.fy[p], a.fz[p]};
+  const float qw = a.w[p] * a.qw_scale;
+  int l0[3], l1[3];
+  float S0[3][NS], S1[3][NS];
+  shapes_both<P>(ci, fo, l0, l1, S0, S1);
+  constexpr int kStag[6] = {1, 2, 4, 6, 5, 3};  // Ex, Ey, Ez, Bx, By, Bz
+  float f[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int m = kStag[c];
+    const int lo[3] = {(m & 1) ? l1[0] : l0[0], (m & 2) ? l1[1] : l0[1], (m & 4) ? l1[2] : l0[2]};
+    f[c] = gather32_one<P>(a.F[c], a, lo, (m & 1) ? S1[0] : S0[0], (m & 2) ? S1[1] : S0[1], (m & 4) ? S1[2] : S0[2]);
+  }
+  float ux, uy, uz;
+  push_u(a, p, f, ux, uy, uz);
+  const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
+  const float v[3] = {ux * ig, uy * ig, uz * ig};
+  int mc[3], nc[3];
+  float mf[3], nf[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float dd = a.dtdx[d] * (v[d] - a.vg[d]);
+    mc[d] = ci[d] + move_offset(fo[d], 0.5f * dd, mf[d]);
+    nc[d] = ci[d] + move_offset(fo[d], dd, nf[d]);
+  }
+  a.cell[p] = (((nc[0] & a.mask[0]) * (int)a.Ny + (nc[1] & a.mask[1])) * (int)a.Nz) + (nc[2] & a.mask[2]);
+  a.fx[p] = nf[0];
+  a.fy[p] = nf[1];
+  a.fz[p] = nf[2];
+  a.ux[p] = ux;
+  a.uy[p] = uy;
+  a.uz[p] = uz;
+  // J^{n+1/2}: component d at its Yee positions
+  shapes_both<P>(mc, mf, l0, l1, S0, S1);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lo[3] = {c == 0 ? l1[0] : l0[0], c == 1 ? l1[1] : l0[1], c == 2 ? l1[2] : l0[2]};
+    deposit32_one<P>(a.J[c], a, lo, c == 0 ? S1[0] : S0[0], c == 1 ? S1[1] : S0[1], c == 2 ? S1[2] : S0[2],
+                     qw * v[c]);
+  }
+  // rho^{n+1} on the nodes
+#pragma unroll
+  for (int d = 0; d < 3; ++d) shape32<P>(nc[d], nf[d], l0[d], S0[d]);
+  deposit32_one<P>(a.rho, a, l0, S0[0], S0[1], S0[2], qw);
+}
+
 // Tiled form: one CTA per chunk of a particle tile (ranges from the last binning;
 // a tile holding more than kTileChunk particles is split into equal chunks so that
 // a dense bunch spreads over many SMs).  The tile's nodal E, B plus guard nodes are
@@ -552,6 +669,15 @@ pic_status launch_push32(pic_ctx* ctx, const Push32Args& a) {
   if (a.n == 0) return PIC_OK;
   const int bs = 256;
   const unsigned nb = (unsigned)((a.n + bs - 1) / bs);
+  if (a.gather && ctx->cycle == PIC_CYCLE_STAGGERED) {
+    switch (ctx->shape_order) {
+      case 1: push32_stag_kernel<1><<<nb, bs, 0, ctx->stream>>>(a); break;
+      case 2: push32_stag_kernel<2><<<nb, bs, 0, ctx->stream>>>(a); break;
+      default: push32_stag_kernel<3><<<nb, bs, 0, ctx->stream>>>(a); break;
+    }
+    PIC_LAUNCH_CHECK(ctx);
+    return PIC_OK;
+  }
   switch (ctx->shape_order) {
     case 1: push32_kernel<1><<<nb, bs, 0, ctx->stream>>>(a); break;
     case 2: push32_kernel<2><<<nb, bs, 0, ctx->stream>>>(a); break;

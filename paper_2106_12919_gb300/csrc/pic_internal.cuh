@@ -187,9 +187,10 @@ pic_status psatd_setup(pic_ctx* ctx);   // 1D tables + per-mode coefficient tabl
 // writes EBh (n+1), Jh (Yee-centered, paper convention) and G = Z * (E or <E>, B or <B>) / Ncell.
 pic_status psatd_update(pic_ctx* ctx, int cur);
 // General form: g_mode 0 -> G = zeta (E,B) / Ncell (nodal), 1 -> G = shift^+ (E,B) / Ncell (Yee);
-// j_yee: Jh already holds the Yee-centered paper-convention spectrum; write_j: store it back.
+// j_yee: Jh already holds the Yee-centered paper-convention spectrum; write_j: store it back;
+// smooth: apply the context's bilinear filter symbols to J, rho^n, rho^{n+1} (the step's deposits).
 pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
-                           int write_j);
+                           int write_j, int smooth);
 // Multiply spectral arrays (plain DFT) by the staggering phase of each component:
 // sign = -1: plain DFT -> paper convention; +1: paper convention -> plain DFT (times scale).
 // comp_kind[c]: 0..5 = Ex..Bz, 6..8 = Jx..Jz, 9 = rho.
@@ -199,7 +200,7 @@ pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, 
 pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale);
 // FP32-form counterparts (FP32 spectra, FP64 tables rounded at use).
 pic_status psatd_update32(pic_ctx* ctx, float2* EB, float2* J, const float2* rn, const float2* rp, float2* G,
-                          int g_mode, int j_yee, int write_j);
+                          int g_mode, int j_yee, int write_j, int smooth);
 pic_status psatd_phase32(pic_ctx* ctx, CP6<float2> in, CP6<float2> out, const int* comp_kind, int ncomp, int sign,
                          double scale);
 pic_status psatd_to_nodal32(pic_ctx* ctx, const float2* EB6, float2* G, double scale);

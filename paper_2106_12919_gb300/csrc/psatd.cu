@@ -281,14 +281,14 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
     J[0] = cscale(J[0], zx);
     J[1] = cscale(J[1], zy);
     J[2] = cscale(J[2], zz);
-    if (u.flt[0]) {
-      // smoothing of the step's deposits: J^{n+1/2}, rho^n, rho^{n+1}
-      const T f = (T)(u.flt[0][ix] * u.flt[1][iy] * u.flt[2][iz]);
+  }
+  if (u.flt[0]) {
+    // smoothing of the step's deposits: J^{n+1/2}, rho^n, rho^{n+1}
+    const T f = (T)(u.flt[0][ix] * u.flt[1][iy] * u.flt[2][iz]);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) J[a] = cscale(J[a], f);
-      rn = cscale(rn, f);
-      rp = cscale(rp, f);
-    }
+    for (int a = 0; a < 3; ++a) J[a] = cscale(J[a], f);
+    rn = cscale(rn, f);
+    rp = cscale(rp, f);
   }
   // [k] x F
   auto cross = [&](const C* F, C* o) {
@@ -607,6 +607,7 @@ pic_status psatd_setup(pic_ctx* ctx) {
         zeta = 1.0;
         shift = make_double2(1.0, 0.0);
       }
+      if (ctx->cycle == PIC_CYCLE_STAGGERED) zeta = 1.0;  // no centering in the staggered cycle
       h[(0 + a) * Nmax + j] = ks;
       h[(3 + a) * Nmax + j] = kc;
       h[(6 + a) * Nmax + j] = zeta;
@@ -675,7 +676,7 @@ static const double2* half_shift(const pic_ctx* ctx, int a) {
 
 template <class C>
 pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C* G, int g_mode, int j_yee,
-                          int write_j) {
+                          int write_j, int smooth) {
   UpdArgs<C> u;
   u.EB = EB;
   u.J = J;
@@ -686,7 +687,7 @@ pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C
   for (int a = 0; a < 3; ++a) {
     u.ks[a] = ctx->ks[a];
     u.zt[a] = ctx->zeta[a];
-    u.flt[a] = ctx->filter_passes > 0 ? ctx->flt[a] : nullptr;
+    u.flt[a] = (smooth && ctx->filter_passes > 0) ? ctx->flt[a] : nullptr;
     u.hs[a] = half_shift(ctx, a);
   }
   u.Ny = ctx->N[1];
@@ -708,17 +709,17 @@ pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C
 }
 
 pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
-                           int write_j) {
-  return psatd_update_t<double2>(ctx, ctx->EBh, ctx->Jh, rn, rp, ctx->G, g_mode, j_yee, write_j);
+                           int write_j, int smooth) {
+  return psatd_update_t<double2>(ctx, ctx->EBh, ctx->Jh, rn, rp, ctx->G, g_mode, j_yee, write_j, smooth);
 }
 
 pic_status psatd_update32(pic_ctx* ctx, float2* EB, float2* J, const float2* rn, const float2* rp, float2* G,
-                          int g_mode, int j_yee, int write_j) {
-  return psatd_update_t<float2>(ctx, EB, J, rn, rp, G, g_mode, j_yee, write_j);
+                          int g_mode, int j_yee, int write_j, int smooth) {
+  return psatd_update_t<float2>(ctx, EB, J, rn, rp, G, g_mode, j_yee, write_j, smooth);
 }
 
 pic_status psatd_update(pic_ctx* ctx, int cur) {
-  return psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], 0, 0, 1);
+  return psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], 0, 0, 1, 1);
 }
 
 template <class C>

@@ -46,7 +46,7 @@ def test_init_rejects_bad_extension_fields():
     from paper_2106_12919_gb300 import pic
     h = ctypes.c_void_p()
     L3, D3, I3 = ctypes.c_int64 * 3, ctypes.c_double * 3, ctypes.c_int32 * 3
-    for field, value in (("filter_passes", 9), ("filter_passes", -1), ("pusher", 2), ("cycle", 2), ("reserved", 1)):
+    for field, value in (("filter_passes", 9), ("filter_passes", -1), ("pusher", 2), ("cycle", 3), ("reserved", 1)):
         e = pic.PicExt()
         pic.LIB.pic_ext_default(ctypes.byref(e))
         setattr(e, field, value)

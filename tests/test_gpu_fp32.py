@@ -157,6 +157,7 @@ CASES = [
     ("beam_wakefield:vay", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 100, False),
     # the nodal comparison cycle
     ("laser_wakefield:nodal", dict(shape=(16, 16, 64), ppc=1), 100, False),
+    ("laser_wakefield:stag", dict(shape=(16, 16, 64), ppc=1), 100, False),
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 100, True),
     ("galilean_drift", dict(shape=(16, 16, 32), ppc=1), 100, True),
 ]
@@ -196,6 +197,8 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
         opts = {"pusher": 1}
     if opt == "nodal":
         opts = {"cycle": 1}
+    if opt == "stag":
+        opts = {"cycle": 2}
     w = workloads.WORKLOADS[name](**kw)
     p = w["params"]
     shape, dx = p["shape"], p["dx"]

@@ -38,6 +38,11 @@ CASES = [
     ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, {"cycle": 1}),
     ("galilean_electrons", dict(shape=(16, 16, 32), ppc=1), 3, {"cycle": 1}),
     ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 3, {"cycle": 1, "pusher": 1}),
+    # the staggered comparison cycle (Sec. 2)
+    ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 4, {"cycle": 2}),
+    ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, {"cycle": 2}),
+    ("galilean_electrons", dict(shape=(16, 16, 32), ppc=1), 3, {"cycle": 2}),
+    ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 3, {"cycle": 2, "filter_passes": 1}),
 ]
 
 

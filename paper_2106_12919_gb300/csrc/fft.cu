@@ -158,7 +158,7 @@ __device__ void fft_tile(C* s, const LAY& lay, int N, const C* __restrict__ tw, 
 
 // z-axis real-to-complex: L lines of Nz reals -> Nz/2+1 complex per line.
 template <class T>
-__global__ void __launch_bounds__(kMaxThreads) fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int Nz,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int Nz,
                                                                int64_t nlines, int L,
                                                                const typename Cplx<T>::type* __restrict__ tw) {
   using C = typename Cplx<T>::type;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kMaxThreads) fft_z_r2c_kernel(CRP6<T> in, CP6<
 
 // z-axis complex-to-real (unnormalised inverse); the imaginary parts of X_0, X_{Nz/2} are ignored.
 template <class T>
-__global__ void __launch_bounds__(kMaxThreads) fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int Nz,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int Nz,
                                                                int64_t nlines, int L,
                                                                const typename Cplx<T>::type* __restrict__ tw) {
   using C = typename Cplx<T>::type;

@@ -186,7 +186,7 @@ __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window
   }
   const int comp = win.comp;
   const float w0 = v0 * win.sj[0], w1 = v1 * win.sj[1], w2 = v2 * win.sj[2], wr = r * win.sr;
-#pragma unroll
+#pragma unroll(P == 3 ? 1 : NS)
   for (int i = 0; i < NS; ++i) {
 #pragma unroll
     for (int jj = 0; jj < NS; ++jj) {
@@ -495,7 +495,9 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     const int gx = lx - go0, gy = ly - go1, gz = lz - go2;
     const bool gin = gx >= 0 && gy >= 0 && gz >= 0 && gx + NS <= t.G[0] && gy + NS <= G1 && gz + NS <= G2;
     if (gin) {
-#pragma unroll
+      // cubic: the outer loop stays rolled (a 4x smaller hot loop for the instruction cache,
+      // measured 6% faster together with the deposit loop); lower orders fully unrolled
+#pragma unroll(P == 3 ? 1 : NS)
       for (int i = 0; i < NS; ++i) {
 #pragma unroll
         for (int jj = 0; jj < NS; ++jj) {

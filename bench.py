@@ -37,6 +37,10 @@ UNIT = "particle-steps/s"
 HBM_PEAK_FALLBACK = 6800.0
 # FP64 FMA units: 152 SMs x 4 FP64 flop/clk/SM x 2.070 GHz (nominal 1.25 TFLOP/s class figure)
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the current
+# kernel version at the full bench size (profiles/push32_tile_laser_wakefield_128x128x512_dram.md);
+# other workloads / forms report null
+MEASURED_TRAFFIC = {("laser_wakefield", (128, 128, 512), "fp32"): 1.438e9}
 # CPU-oracle sample: the same workload on a 1/64-volume box (same dx, dt, physics)
 SAMPLE_SHAPE = {"laser_wakefield": (32, 32, 128), "beam_wakefield": (64, 64, 128),
                 "thermal_plasma": (32, 32, 32), "galilean_drift": (32, 32, 64), "seed_wave": (32, 32, 32)}
@@ -355,9 +359,10 @@ def run_form(form, w, args, world, rank, local):
         # 32 B read + 28 B written per particle; nodal E, B read (24 B) and J, rho deposited (16 B) per cell
         nbytes = 60 * per_launch + 40 * ncell
         achieved = nbytes / push_avg_s / 1e9
+        traffic = MEASURED_TRAFFIC.get((w["name"].rsplit("_", 1)[0], tuple(shape), form))
         roofline = {"kernel": "push32_tile_kernel (gather + Boris + deposit)", "bound": "hbm", "achieved": achieved,
-                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                    "algorithmic_bytes": "60 B/particle + 40 B/cell per launch"}
+                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                    "algorithmic_bytes": "60 B/particle + 40 B/cell per launch (%.3g B)" % nbytes}
     else:
         flops = push_flops_per_particle(p["shape_order"]) * per_launch
         achieved = flops / push_avg_s / 1e12

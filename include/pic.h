@@ -88,7 +88,7 @@ typedef enum {
  *   precision: PIC_FP64 (the pic_step family) or PIC_FP32 (the pic_step32 family).
  *   c, eps0: speed of light and vacuum permittivity.  Defaults 1, 1.
  *   tile[3]: particle tile edge in cells per axis for binning (powers of two
- *     dividing the grid).  Default 4, 8, 8.
+ *     dividing the grid).  Default 8, 8, 8.
  *   sort_interval: re-bin the particles every this many steps inside pic_step
  *     (0 = never).  Default 20.
  *   cuda_stream: a cudaStream_t; NULL = legacy default stream.

@@ -131,8 +131,7 @@ void pic_ext_default(pic_ext* e) {
   e->precision = PIC_FP64;
   e->c = 1.0;
   e->eps0 = 1.0;
-  e->tile[0] = 4;
-  e->tile[1] = e->tile[2] = 8;
+  e->tile[0] = e->tile[1] = e->tile[2] = 8;
   e->sort_interval = 20;
   e->cuda_stream = nullptr;
 }

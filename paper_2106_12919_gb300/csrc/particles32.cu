@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(256) push32_stag_kernel(Push32Args a) {
 //
 // Shared-memory layout.  Binning orders the cells of a tile z fastest, then x, then y,
 // so at P particles per cell the 32 lanes of a warp (visiting every P-th particle)
-// hold 32 cells: all T2 = 8 z-cells of T0 = 4 x-planes at one y.  Both shared arrays
+// hold 32 cells: the T2 = 8 z-cells of 4 consecutive x-planes at one y.  Both shared arrays
 // are component-planar with the plane stride padded to 8 (mod 32) words, so the
 // lanes' addresses for the same relative node fall in 32 distinct banks: every
 // gather load and every deposit atomic of such a warp is one conflict-free access.

@@ -244,7 +244,7 @@ class Context:
 
     def __init__(self, shape, dx, dt, shape_order, centering_order, variant=STANDARD,
                  v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0,
-                 tile=(4, 8, 8), sort_interval=20, stream=None, precision=PIC_FP64, filter_passes=0,
+                 tile=(8, 8, 8), sort_interval=20, stream=None, precision=PIC_FP64, filter_passes=0,
                  pusher=0, cycle=0):
         self.shape = tuple(int(n) for n in shape)
         self.ncell = self.shape[0] * self.shape[1] * self.shape[2]

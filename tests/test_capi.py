@@ -37,7 +37,7 @@ def test_ext_defaults():
     e = pic.PicExt()
     pic.LIB.pic_ext_default(ctypes.byref(e))
     assert e.struct_size == ctypes.sizeof(pic.PicExt)
-    assert (e.c, e.eps0, list(e.tile), e.sort_interval) == (1.0, 1.0, [4, 8, 8], 20)
+    assert (e.c, e.eps0, list(e.tile), e.sort_interval) == (1.0, 1.0, [8, 8, 8], 20)
     assert (e.filter_passes, e.pusher, e.cycle, e.reserved) == (0, pic.PIC_PUSHER_BORIS, pic.PIC_CYCLE_HYBRID, 0)
 
 

@@ -281,8 +281,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(
 
 // In-place C2C along a strided axis: element e of column col of outer line o of
 // component c at p[c] + o * os + e * es + col.  A CTA takes W adjacent columns.
-template <bool INV, class C>
-__global__ void __launch_bounds__(kMaxThreads) fft_strided_kernel(CP6<C> data, int N, int64_t es, int64_t os,
+// MAXT: the block size bound; the common 256-thread launches (N <= 128 with 16 columns) are
+// compiled for 5 resident CTAs per SM in FP32 (48 registers, no spills) and 4 in FP64, larger ones
+// for one.
+template <bool INV, class C, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? (sizeof(C) == 8 ? 5 : 4) : 1) fft_strided_kernel(CP6<C> data, int N, int64_t es, int64_t os,
                                                                  int ncols, int W, const C* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -334,10 +337,14 @@ pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp)
   dim3 grid((nzh + W - 1) / W, (unsigned)nouter, ncomp);
   const int threads = W * N / 8;
   const size_t smem = (size_t)W * N * sizeof(C);
-  if (inv)
-    fft_strided_kernel<true, C><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, twiddles<C>(ctx, axis));
-  else
-    fft_strided_kernel<false, C><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, twiddles<C>(ctx, axis));
+  const C* tw = twiddles<C>(ctx, axis);
+  if (threads <= 256) {
+    if (inv) fft_strided_kernel<true, C, 256><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
+    else fft_strided_kernel<false, C, 256><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
+  } else {
+    if (inv) fft_strided_kernel<true, C, kMaxThreads><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
+    else fft_strided_kernel<false, C, kMaxThreads><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
+  }
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
@@ -351,8 +358,12 @@ pic_status set_smem_attrs(pic_ctx* ctx) {
   PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
   PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
   const int ssm = 8192 * (int)sizeof(C);
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<false, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<true, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<false, C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<true, C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<false, C, kMaxThreads>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<true, C, kMaxThreads>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
   return PIC_OK;
 }
 

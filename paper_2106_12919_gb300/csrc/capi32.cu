@@ -233,7 +233,8 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     const bool last = s == nsteps - 1;
     // Binning: the tiled push needs each species' tile ranges.  The first step of a call and
     // every sort_interval-th step re-bin unconditionally; in between, the device re-bins only
-    // when more than 2 % of the particles left their tile window in the previous push.
+    // when the previous push moved more than 2 % of the particles out of their tile (they would
+    // gather from global memory in the next push).
     if (tiled) {
       const int force = (s == 0 || since_forced >= ctx->sort_interval) ? 1 : 0;
       since_forced = force ? 1 : since_forced + 1;

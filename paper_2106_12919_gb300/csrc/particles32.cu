@@ -402,7 +402,7 @@ struct TileArgs {
   const uint32_t* chunk;  // [n_tiles + 1] exclusive prefix sum of chunks per tile
   const uint32_t* chunk_tile;  // tile of each chunk
   int64_t n_tiles;
-  unsigned long long* outside;  // count of particles that used the global-memory path
+  unsigned long long* outside;  // count of particles whose new cell left the chunk's tile
   int T[3];               // tile edge (cells)
   int nt[3];              // tiles per axis
   int cpt;                // cells per tile
@@ -531,7 +531,6 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
           }
         }
       }
-      ++nout;
     }
     float ux, uy, uz;
     push_u(a, p, f, ux, uy, uz);
@@ -541,6 +540,13 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     float nfx, nfy, nfz;
     const int nx = ix + move_offset(fx, dX, nfx), ny = iy + move_offset(fy, dY, nfy),
               nz = iz + move_offset(fz, dZ, nfz);
+    // the next push gathers this particle from the staged nodes of this tile only while its new
+    // cell stays in the tile: count those that leave (the device re-bins before the next push
+    // when they exceed 2 % of all particles)
+    nout += ((unsigned)(nx - (go0 + 1)) >= (unsigned)t.T[0] || (unsigned)(ny - (go1 + 1)) >= (unsigned)t.T[1] ||
+             (unsigned)(nz - (go2 + 1)) >= (unsigned)t.T[2])
+                ? 1u
+                : 0u;
     a.cell[p] = (((nx & a.mask[0]) * (int)a.Ny + (ny & a.mask[1])) * (int)a.Nz) + (nz & a.mask[2]);
     a.fx[p] = nfx;
     a.fy[p] = nfy;
@@ -606,9 +612,8 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     float mfx, mfy, mfz;
     const int mx = nx + move_offset(nfx, hX, mfx), my = ny + move_offset(nfy, hY, mfy),
               mz = nz + move_offset(nfz, hZ, mfz);
-    const bool jin = deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
-    const bool rin = deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
-    nout += (jin && rin) ? 0u : 1u;
+    deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
+    deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
   }
   nout = __reduce_add_sync(0xffffffffu, nout);
   if (nout && (threadIdx.x & 31) == 0) atomicAdd(t.outside, (unsigned long long)nout);
@@ -757,7 +762,7 @@ __global__ void fill_u32_kernel(uint32_t* p, int64_t n, uint32_t v, const int* g
     p[e] = v;
 }
 
-// gate = (particles outside their tile window in the last push) > limit, or forced; resets the count
+// gate = (particles whose new cell left their tile in the last push) > limit, or forced; resets the count
 __global__ void bin_decide_kernel(int* gate, unsigned long long* outside, unsigned long long limit, int force) {
   *gate = (force || *outside > limit) ? 1 : 0;
   *outside = 0ull;

@@ -126,7 +126,7 @@ struct pic_ctx {
   uint32_t* cell_cursor;  // FP32 binning: per-cell scatter cursors
   double* adj_work;       // reverse mode: rhobar^n, rhobar^{n+1}, 6 nodal force adjoints
   int* bin_gate;                    // FP32 form: device flag "re-bin before the next push"
-  unsigned long long* bin_outside;  // FP32 form: particles that left their tile window in the last push
+  unsigned long long* bin_outside;  // FP32 form: particles whose new cell left their tile in the last push
 
   int64_t steps_done;
   // FP32 form: per-species tile ranges of the last binning inside pic_step32
@@ -271,7 +271,7 @@ pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const 
 // chunks_out (optional, tile_chunk_words entries): chunk starts for particles_push32_tiled.
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate = nullptr,
                            uint32_t* chunks_out = nullptr);
-// *bin_gate = (particles outside their tile window in the last tiled push > 2 % of total) || force
+// *bin_gate = (particles whose new cell left their tile in the last tiled push > 2 % of total) || force
 pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force);
 
 // center.cu -------------------------------------------------------------------

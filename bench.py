@@ -119,6 +119,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest value of x over the ranks of the job (replicas: the slowest rank sets the
+    time); x itself when running alone."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, world, ms_max):
+    """Whole-job units per second: every rank processed units_per_rank per step (weak scaling,
+    independent replicas) and the job took the slowest rank's time."""
+    return units_per_rank * steps * world / (ms_max * 1e-3)
+
+
 def run_oracle_sample(name, steps):
     """Oracle (FP64 CPU) on the 1/64-volume sample box: returns (particle-steps/s, description)."""
     from oracle import step
@@ -315,11 +333,8 @@ def run_form(form, w, args, world, rank, local):
     clocks = sampler.stop()
     stage = {s: ctx.timing_read(s) for s in ("push", "fft", "update", "bin", "other", "all")}
     ctx.timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = npart * args.steps * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, world)
+    value = job_throughput(npart, args.steps, world, ms)
 
     # ---- end to end: host (pinned) state -> device, one pic_step, field energy back ----
     # Every step copies its whole input state (E, B, rho and all particle arrays) from pinned host
@@ -378,11 +393,8 @@ def run_form(form, w, args, world, rank, local):
     t1.synchronize()
     e2e_ms = t0.elapsed_time(t1)
     del E2, B2, rho2, sp2, bufs, J2, sets
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": npart * ke * world / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_ms = max_over_ranks(e2e_ms, world)
+    e2e = {"value": job_throughput(npart, ke, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": 8, "steps": ke,
            "note": "per step: pinned H2D of E, B, rho and all particles (double-buffered: the copy of "
                    "step k+1 overlaps step k), pic_step(1), field energy read back"}

@@ -222,6 +222,17 @@ struct TableArgs {
   GaussLegendre gl;
 };
 
+// Mode index m -> (ix, iy, iz) for the [Nx][Ny][Nz/2+1] spectra; 32-bit arithmetic (every context
+// has fewer than 2^32 modes), Ny a power of two.
+__device__ __forceinline__ void mode_xyz(int64_t m, uint32_t nzh, int lgNy, uint32_t& ix, uint32_t& iy,
+                                         uint32_t& iz) {
+  const uint32_t mm = (uint32_t)m;
+  const uint32_t r = mm / nzh;
+  iz = mm - r * nzh;
+  iy = r & ((1u << lgNy) - 1u);
+  ix = r >> lgNy;
+}
+
 __global__ void build_tables_kernel(TableArgs t) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= t.nmode) return;
@@ -465,21 +476,26 @@ struct PhaseArgs {
   int64_t Ny, nzh, nmode;
 };
 
-// phase factors are formed in FP64 and rounded once
+// The phase factors are formed in the data precision from the FP64 1D tables (GB300's FP64 rate is
+// a small fraction of its FP32 rate; in the FP32 form a product of up to three unit phases in FP32
+// is accurate to a few 1e-7, far below the transforms' own rounding).
 template <class C>
 __global__ void phase_kernel(PhaseArgs<C> p) {
+  using T = decltype(C().x);
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= p.nmode) return;
   const int c = blockIdx.y;
-  const int64_t iz = m % p.nzh, r = m / p.nzh;
-  const int64_t iy = r % p.Ny, ix = r / p.Ny;
-  double2 f = make_double2(p.scale, 0.0);
+  uint32_t ix, iy, iz;
+  mode_xyz(m, (uint32_t)p.nzh, __ffsll(p.Ny) - 1, ix, iy, iz);
+  C f;
+  f.x = (T)p.scale;
+  f.y = (T)0;
   const int mk = p.mask[c];
-  if (mk & 1) f = cmul(f, p.hs[0][ix]);
-  if (mk & 2) f = cmul(f, p.hs[1][iy]);
-  if (mk & 4) f = cmul(f, p.hs[2][iz]);
+  if (mk & 1) f = cmul(f, cast_c<C>(p.hs[0][ix]));
+  if (mk & 2) f = cmul(f, cast_c<C>(p.hs[1][iy]));
+  if (mk & 4) f = cmul(f, cast_c<C>(p.hs[2][iz]));
   if (p.sign > 0) f.y = -f.y;
-  p.out.p[c][m] = cmul(p.in.p[c][m], cast_c<C>(f));
+  p.out.p[c][m] = cmul(p.in.p[c][m], f);
 }
 
 template <class C>
@@ -493,17 +509,18 @@ struct NodalArgs {
 
 template <class C>
 __global__ void to_nodal_kernel(NodalArgs<C> a) {
+  using T = decltype(C().x);
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= a.nmode) return;
   const int c = blockIdx.y;
-  const int64_t iz = m % a.nzh, r = m / a.nzh;
-  const int64_t iy = r % a.Ny, ix = r / a.Ny;
+  uint32_t ix, iy, iz;
+  mode_xyz(m, (uint32_t)a.nzh, __ffsll(a.Ny) - 1, ix, iy, iz);
   const int mk = stag_mask(c);
-  double z = a.scale;
-  if (mk & 1) z *= a.zt[0][ix];
-  if (mk & 2) z *= a.zt[1][iy];
-  if (mk & 4) z *= a.zt[2][iz];
-  a.G[c * a.nmode + m] = cscale(a.EB[c * a.nmode + m], (decltype(C().x))z);
+  T z = (T)a.scale;
+  if (mk & 1) z *= (T)a.zt[0][ix];
+  if (mk & 2) z *= (T)a.zt[1][iy];
+  if (mk & 4) z *= (T)a.zt[2][iz];
+  a.G[c * a.nmode + m] = cscale(a.EB[c * a.nmode + m], z);
 }
 
 // ---------------------------------------------------------------------------

@@ -9,8 +9,8 @@
 //
 // Every CTA loads a whole tile of lines into shared memory, runs the radix-8
 // (+ one radix-4 or radix-2) Stockham passes there, and writes the tile back.
-// z lines are contiguous (line-major tile, padded one slot per 8 elements to
-// keep the radix-8 scatter conflict-free); y and x lines are strided, so a CTA
+// z lines are contiguous (line-major tile, padded one slot per 16 elements to
+// spread the radix-8 scatter over the banks); y and x lines are strided, so a CTA
 // takes W adjacent columns (consecutive k_z) and the tile is element-major,
 // which keeps the global loads coalesced in W-element rows.
 #include "pic_internal.cuh"
@@ -19,15 +19,16 @@
 
 namespace {
 
+constexpr int kZPadShift = 4;  // z-pass lines padded one slot per 16 elements (measured best of 4..32)
 constexpr int kZTile = 4096;    // complex elements per z-pass CTA (L lines * Nz/2)
 constexpr int kMaxThreads = 1024;
 
 // All sizes are powers of two: index arithmetic uses shifts and masks (lg* = log2).
 __device__ __forceinline__ int lg2(int v) { return __ffs(v) - 1; }
 
-struct LayLine {  // z pass: element e of line l at l * LP + e + e / 8
+struct LayLine {  // z pass: element e of line l at l * LP + e + e / 16
   int LP;
-  __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + (e >> 3); }
+  __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + (e >> kZPadShift); }
   // butterfly b of nb = 2^lgnb per line -> line l, index j
   __device__ __forceinline__ void map(int b, int lgnb, int& l, int& j) const {
     l = b >> lgnb;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_r2c_kernel(
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int M = Nz / 2;
-  const LayLine lay{M + M / 8};
+  const LayLine lay{M + (M >> kZPadShift)};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
   const C* src = reinterpret_cast<const C*>(in.p[comp]);
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int M = Nz / 2;
-  const LayLine lay{M + M / 8};
+  const LayLine lay{M + (M >> kZPadShift)};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
   const C* srcb = in.p[comp];
@@ -354,7 +355,7 @@ int z_lines_per_cta(int Nz) { return kZTile / (Nz / 2); }
 template <class T>
 pic_status set_smem_attrs(pic_ctx* ctx) {
   using C = typename Cplx<T>::type;
-  const int zsm = kZTile * 9 / 8 * (int)sizeof(C);
+  const int zsm = (kZTile + (kZTile >> kZPadShift)) * (int)sizeof(C);
   PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
   PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
   const int ssm = 8192 * (int)sizeof(C);
@@ -417,7 +418,7 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
-  const size_t smem = (size_t)L * (Nz / 2 + Nz / 16) * sizeof(C);
+  const size_t smem = (size_t)L * (Nz / 2 + ((Nz / 2) >> kZPadShift)) * sizeof(C);
   fft_z_r2c_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
@@ -436,7 +437,7 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
-  const size_t smem = (size_t)L * (Nz / 2 + Nz / 16) * sizeof(C);
+  const size_t smem = (size_t)L * (Nz / 2 + ((Nz / 2) >> kZPadShift)) * sizeof(C);
   fft_z_c2r_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;

@@ -21,7 +21,7 @@ momentum per unit mass, u = gamma v.  In the Galilean variant the particle
 moves by dt (v - v_gal) on the grid (Galilean coordinates x = x' - v_gal t,
 App. A.2), while force and current use the lab velocity v.
 
-Direct deposition (Sec. 2 cycle, deposit on the nodal grid; App. A.4 takes J
+Direct deposition (Sec. 2 cycle, deposit on the nodal grid; App. A.5 takes J
 constant over the step): J^{n+1/2} = sum_p q w v^{n+1/2} S(x^{n+1/2} - x_i) / dV with
 x^{n+1/2} = x^n + dt (v - v_gal) / 2, and rho^{n+1} = sum_p q w S(x^{n+1} - x_i) / dV.
 """

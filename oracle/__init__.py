@@ -21,7 +21,9 @@ grid         Yee staggering, discrete Fourier conventions (App. A.1) and the
 psatd        Standard / Galilean / averaged-Galilean PSATD coefficients and
              k-space updates (Sec. 4.2-4.4).
 particles    B-spline shapes, gather, Boris push, direct deposition, tile bins.
-step         The hybrid PIC cycle of Sec. 2.
+step         The hybrid PIC cycle of Sec. 2 (and its comparison and FDTD cycles).
+fdtd         Yee finite-difference Maxwell solver of order 2m (the FDTD form of the
+             hybrid scheme, Sec. 6).
 diagnostics  Field energy (Sec. 2 (iii)), the L2 error norm (Sec. 5.2), the stencil
              extent (Eq. stencil_extent), the beam RMS (Eq. RMS_pwfa) and the numerical
              vacuum dispersion of an update (Sec. 2 (i), App. B).

@@ -15,6 +15,10 @@ nodes, the centered modified wave numbers [k]_c in the solver, no centering; STA
 Yee-grid solver of the hybrid cycle, with E, B gathered from and J deposited at their own Yee
 positions (rho nodal), no centering.
 
+Hybrid FDTD cycle (the FDTD adaptation the conclusions of Sec. 6 point to): the hybrid cycle with
+step 5 replaced by the Yee finite-difference update of oracle/fdtd.py (order 2m per axis from the
+spectral-order argument, 0 meaning Yee's order 2); rho^n, rho^{n+1} are not used by the solver.
+
 Averaged Galilean variant (Sec. 4.4): the Yee state E, B evolves with the
 Galilean update; the averaged fields <E>^{n+1}, <B>^{n+1} computed alongside are
 what the next step gathers (they replace E, B in step 1).  The first step gathers
@@ -22,10 +26,10 @@ E^0, B^0.
 """
 import numpy as np
 
-from . import grid, particles, psatd
+from . import fdtd, grid, particles, psatd
 
 STANDARD, GALILEAN, AVERAGED = 0, 1, 2
-HYBRID, NODAL, STAGGERED = 0, 1, 2
+HYBRID, NODAL, STAGGERED, HYBRID_FDTD = 0, 1, 2, 3
 
 
 class Params:
@@ -46,9 +50,14 @@ class Params:
         self.eps0 = float(eps0)
         self.filter_passes = int(filter_passes)
         self.pusher = int(pusher)        # 0: Boris, 1: Vay
-        self.cycle = int(cycle)          # HYBRID (Sec. 2), or the NODAL or STAGGERED comparison cycle
+        self.cycle = int(cycle)          # HYBRID (Sec. 2), the NODAL or STAGGERED comparison cycle,
+                                         # or HYBRID_FDTD
         self._co = None
         self._k = None
+
+    def fd_orders(self):
+        """Finite-difference order per axis of the FDTD solver (0 -> 2, Yee)."""
+        return tuple(o if o else 2 for o in self.spectral_order)
 
     def coefficients(self):
         if self._co is None:
@@ -128,7 +137,11 @@ def hybrid_step(p, state):
         Jy = Jf
     else:
         Jy = [grid.center_to_yee(Jf[a], grid.J_NAMES[a], o) for a in range(3)]         # step 4
-    E, B, avg, im = maxwell_update(p, state["E"], state["B"], Jy, rn_f, rp_f)           # step 5
+    if p.cycle == HYBRID_FDTD:                                                        # step 5
+        E, B = fdtd.yee_update(state["E"], state["B"], Jy, p.dt, p.fd_orders(), p.dx, p.c, p.eps0)
+        avg, im = None, 0.0
+    else:
+        E, B, avg, im = maxwell_update(p, state["E"], state["B"], Jy, rn_f, rp_f)
     state.update(E=E, B=B, J=Jy, rho=rho_np1, species=new_species, max_imag=im)
     if avg is not None:
         state["avg"] = avg

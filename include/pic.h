@@ -76,8 +76,12 @@ typedef enum {
   PIC_CYCLE_HYBRID = 0,  /* the hybrid nodal-staggered cycle of Sec. 2 (the method) */
   PIC_CYCLE_NODAL = 1,   /* the nodal comparison cycle of Sec. 2: every quantity on the nodes,
                             [k]_c in the solver, no centering */
-  PIC_CYCLE_STAGGERED = 2  /* the staggered comparison cycle of Sec. 2: the Yee-grid solver, E, B
+  PIC_CYCLE_STAGGERED = 2, /* the staggered comparison cycle of Sec. 2: the Yee-grid solver, E, B
                               gathered from and J deposited at their own Yee positions, no centering */
+  PIC_CYCLE_HYBRID_FDTD = 3 /* the hybrid scheme with an FDTD solver (the adaptation to FDTD the
+                               conclusions of Sec. 6 state): nodal gather / deposit and the
+                               finite-order centering of Sec. 3 around a Yee finite-difference
+                               update of order 2m, no Fourier transforms */
 } pic_cycle;
 
 /*
@@ -104,7 +108,17 @@ typedef enum {
  *     and zeta_F = 1.  With PIC_CYCLE_STAGGERED the fields stay on the Yee grid throughout:
  *     the shapes of each component are taken on its own staggered grid (offset 1/2 cell
  *     along its staggered axes) for the gather of E, B and the deposit of J (rho nodal), and
- *     zeta_F = 1.  The FP32 form then uses the untiled push.  Default PIC_CYCLE_HYBRID.
+ *     zeta_F = 1.  The FP32 form then uses the untiled push.  With PIC_CYCLE_HYBRID_FDTD
+ *     the fields advance in real space on the Yee grid by leapfrog with the B update split
+ *     in halves (B^{n+1/2} = B^n - (dt/2) curl E^n; E^{n+1} = E^n + dt (c^2 curl B^{n+1/2}
+ *     - J^{n+1/2} / eps0); B^{n+1} = B^{n+1/2} - (dt/2) curl E^{n+1}), each derivative the
+ *     staggered difference sum_n c_n (f_{j+n} - f_{j-n+1}) / dx with c_n = alpha^s_{m,n} /
+ *     (2n - 1), 2m = spectral_order of the axis (0 means 2: Yee's scheme), whose symbol is
+ *     i [k]_s.  E, B are centered to the nodes and J to the Yee grid by the stencils of Sec. 3
+ *     (Eq. staggered_finite_sum) in real space.  rho is deposited (rho^{n+1} on exit) but the
+ *     solver does not use it.  Requires PIC_PSATD_STANDARD and filter_passes = 0
+ *     (PIC_ERR_UNSUPPORTED otherwise) and dt within the Courant limit
+ *     c dt sqrt(sum_a max_k [k_a]_s^2) <= 2 (PIC_ERR_ARG otherwise).  Default PIC_CYCLE_HYBRID.
  *   reserved: must be 0.
  */
 typedef struct {
@@ -299,6 +313,8 @@ pic_status pic_fft_inverse(pic_ctx* ctx, double* const spec[], double* const rea
  * Yee E^n, B^n, J^{n+1/2} (Yee), rho^n, rho^{n+1} (nodal) -> Yee E^{n+1}, B^{n+1}
  * (in place).  For the averaged variant, Eavg[3], Bavg[3] (may be NULL for the
  * other variants) receive <E>^{n+1}, <B>^{n+1} at the Yee positions.
+ * On a PIC_CYCLE_HYBRID_FDTD context this is the finite-difference leapfrog step
+ * described under pic_ext.cycle; rho_n and rho_np1 are not read and may be NULL.
  * Asynchronous.
  */
 pic_status pic_maxwell_step(pic_ctx* ctx, double* const E[3], double* const B[3],
@@ -401,7 +417,8 @@ pic_status pic_stencil_extent(pic_ctx* ctx, const char* coef, int axis, double* 
  * Nyquist index at -N_a/2): ks = [k]_s and kc = [k]_c at the context's spectral order
  * (Sec. 4.1, Eqs. k_staggered / k_centered) and zeta = zeta_F, the Fourier symbol of the
  * centering of order centering_order[a] (App. C).  Nodal cycle: ks = kc = the solver's
- * [k]_c and zeta = 1; staggered cycle: zeta = 1.  Any pointer may be NULL.  Synchronous.
+ * [k]_c and zeta = 1; staggered cycle: zeta = 1; FDTD cycle: ks = the symbol of the
+ * finite difference (order 2 when spectral_order is 0).  Any pointer may be NULL.  Synchronous.
  */
 pic_status pic_axis_tables(pic_ctx* ctx, int axis, double* ks, double* kc, double* zeta);
 
@@ -410,8 +427,9 @@ pic_status pic_axis_tables(pic_ctx* ctx, int axis, double* ks, double* kc, doubl
  * along axis a (Sec. 2 (i), App. B): per Fourier index along the axis (the other two
  * indices 0) the transverse block of the update, [[TC, -i c^2 TS [k]_s], [-i TS [k]_s, TC]],
  * has eigenvalues TC +- i c TS [k]_s; omega = (larger eigenvalue phase) / dt.  Standard
- * PSATD gives omega = c |[k]_s|; Galilean phases are shifted by Omega_c dt.  omega: HOST,
- * N_a doubles, FFT order.  Synchronous.
+ * PSATD gives omega = c |[k]_s|; Galilean phases are shifted by Omega_c dt.  FDTD cycle:
+ * the leapfrog's omega = (2 / dt) asin(c dt |[k]_s| / 2).  omega: HOST, N_a doubles, FFT
+ * order.  Synchronous.
  */
 pic_status pic_vacuum_dispersion(pic_ctx* ctx, int axis, double* omega);
 

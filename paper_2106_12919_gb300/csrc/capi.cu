@@ -40,12 +40,6 @@ pic_status dalloc(pic_ctx* ctx, T** p, size_t count, const char* what) {
   return PIC_OK;
 }
 
-#define PIC_TRY(x)                      \
-  do {                                  \
-    pic_status s_ = (x);                \
-    if (s_ != PIC_OK) return s_;        \
-  } while (0)
-
 pic_status check_species(pic_ctx* ctx, const pic_species* sp, int n_species) {
   if (n_species < 0 || (n_species > 0 && sp == nullptr)) return pic_set_error(ctx, PIC_ERR_ARG, "species array");
   for (int s = 0; s < n_species; ++s) {
@@ -193,7 +187,10 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   if (!(e.c > 0.0) || !(e.eps0 > 0.0)) return fail(PIC_ERR_ARG, "c and eps0 must be > 0");
   if (e.filter_passes < 0 || e.filter_passes > 8) return fail(PIC_ERR_ARG, "filter_passes must be in [0, 8]");
   if (e.pusher != PIC_PUSHER_BORIS && e.pusher != PIC_PUSHER_VAY) return fail(PIC_ERR_ARG, "unknown pusher");
-  if (e.cycle < PIC_CYCLE_HYBRID || e.cycle > PIC_CYCLE_STAGGERED) return fail(PIC_ERR_ARG, "unknown cycle");
+  if (e.cycle < PIC_CYCLE_HYBRID || e.cycle > PIC_CYCLE_HYBRID_FDTD) return fail(PIC_ERR_ARG, "unknown cycle");
+  if (e.cycle == PIC_CYCLE_HYBRID_FDTD &&
+      (psatd_variant != PIC_PSATD_STANDARD || e.filter_passes != 0 || e.precision != PIC_FP64))
+    return fail(PIC_ERR_UNSUPPORTED, "the FDTD cycle takes the standard variant, no filter, FP64");
   if (e.reserved) return fail(PIC_ERR_ARG, "reserved fields must be 0");
   if (psatd_variant != PIC_PSATD_STANDARD) {
     if (!v_gal) return fail(PIC_ERR_ARG, "v_gal required");
@@ -220,6 +217,11 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   ctx->cycle = e.cycle;
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) ctx->sp_off_n[q] = -1;
   ctx->stream = reinterpret_cast<cudaStream_t>(e.cuda_stream);
+  if (ctx->cycle == PIC_CYCLE_HYBRID_FDTD && (st = fdtd_setup(ctx)) != PIC_OK) {
+    fprintf(stderr, "pic_init: %s\n", ctx->err);
+    pic_destroy(ctx);
+    return st;
+  }
   ctx->ncell = grid[0] * grid[1] * grid[2];
   ctx->nzh = grid[2] / 2 + 1;
   ctx->nmode = grid[0] * grid[1] * ctx->nzh;
@@ -333,8 +335,13 @@ pic_status pic_maxwell_step(pic_ctx* ctx, double* const E[3], double* const B[3]
                             double* const Bavg[3]) {
   if (!ctx) return PIC_ERR_ARG;
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
-  if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || !all_nonnull(J, 3) || !rho_n || !rho_np1)
+  if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || !all_nonnull(J, 3))
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
+  if (ctx->cycle == PIC_CYCLE_HYBRID_FDTD) {
+    const double* cJ[3] = {J[0], J[1], J[2]};
+    return fdtd_update(ctx, E, B, cJ);
+  }
+  if (!rho_n || !rho_np1) return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   const bool avg = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN;
   if (avg && (!all_nonnull(Eavg, 3) || !all_nonnull(Bavg, 3)))
     return pic_set_error(ctx, PIC_ERR_ARG, "averaged variant needs Eavg, Bavg");
@@ -417,6 +424,7 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
   if (nsteps < 0) return pic_set_error(ctx, PIC_ERR_ARG, "nsteps < 0");
   PIC_TRY(check_species(ctx, sp, n_species));
   if (nsteps == 0) return PIC_OK;
+  if (ctx->cycle == PIC_CYCLE_HYBRID_FDTD) return fdtd_step(ctx, E, B, J, rho, sp, n_species, nsteps);
   const int64_t nm = ctx->nmode, nc = ctx->ncell;
   // entry: spectral E^n, B^n, rho^n; nodal gather fields
   const double* cE[3] = {E[0], E[1], E[2]};

@@ -92,9 +92,14 @@ __global__ void extent_dft_kernel(const double2* PQ, int64_t N, int axis, double
 // [[TC, -i c^2 TS k], [-i TS k, TC]], has eigenvalues TC +- i c TS k; omega = (largest phase)/dt.
 // Along z only m <= Nz/2 is stored: the table at -k is the conjugate, which negates both phases.
 __global__ void dispersion_kernel(const double2* TC, const double2* TS, const double* ks, int64_t Ny, int64_t Nz,
-                                  int64_t N, int axis, double c, double dt, double* out) {
+                                  int64_t N, int axis, double c, double dt, int fdtd, double* out) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= N) return;
+  if (fdtd) {
+    // leapfrog: sin(omega dt / 2) = c dt [k]_s / 2 (within the Courant limit checked at creation)
+    out[m] = 2.0 * asin(fmin(1.0, 0.5 * c * dt * fabs(ks[m]))) / dt;
+    return;
+  }
   const int64_t nzh = Nz / 2 + 1;
   const bool mirror = axis == 2 && m > N / 2;
   const int64_t mm = mirror ? N - m : m;
@@ -250,7 +255,7 @@ pic_status pic_vacuum_dispersion(pic_ctx* ctx, int axis, double* omega) {
   double* d = reinterpret_cast<double*>(ctx->G);
   dispersion_kernel<<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(
       ctx->coef + COEF_TC * ctx->nmode, ctx->coef + COEF_TS * ctx->nmode, ctx->ks[axis], ctx->N[1], ctx->N[2], N,
-      axis, ctx->c, ctx->dt, d);
+      axis, ctx->c, ctx->dt, ctx->cycle == PIC_CYCLE_HYBRID_FDTD ? 1 : 0, d);
   PIC_LAUNCH_CHECK(ctx);
   PIC_CUDA_TRY(ctx, cudaMemcpyAsync(omega, d, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   PIC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));

@@ -91,6 +91,7 @@ struct pic_ctx {
   int64_t ncell, nzh, nmode;
   int ncoef;
   CenterWeights cw[3];
+  CenterWeights fdw[3];  // FDTD cycle: staggered-difference weights alpha^s_{m,n} / ((2n - 1) dx)
 
   // device tables
   double* k1d;       // [3][Nmax] ks, then [3][Nmax] kc, then [3][Nmax] zeta
@@ -164,6 +165,12 @@ pic_status pic_set_error(pic_ctx* ctx, pic_status st, const char* fmt, ...);
                            cudaGetErrorString(e_));                                  \
   } while (0)
 
+#define PIC_TRY(x)               \
+  do {                           \
+    pic_status s_ = (x);         \
+    if (s_ != PIC_OK) return s_; \
+  } while (0)
+
 // Component pointer bundles passed by value to kernels.
 template <class T> struct RP6 { T* p[6]; };
 template <class T> struct CRP6 { const T* p[6]; };
@@ -182,6 +189,7 @@ template <class T>
 pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp);
 
 // psatd.cu -------------------------------------------------------------------
+long double fornberg_alpha_s(int m, int n);  // alpha^s_{m,n} (Eq. eq_Fornberg_staggered), host
 pic_status psatd_setup(pic_ctx* ctx);   // 1D tables + per-mode coefficient tables
 // Spectral update of one step. Reads ctx->EBh, ctx->Jh (nodal DFT of J), rhoh[cur], rhoh[1-cur];
 // writes EBh (n+1), Jh (Yee-centered, paper convention) and G = Z * (E or <E>, B or <B>) / Ncell.
@@ -277,6 +285,16 @@ pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int for
 // center.cu -------------------------------------------------------------------
 pic_status center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);
 pic_status center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* const out[3]);
+
+// fdtd.cu ---------------------------------------------------------------------
+// Weights of the FDTD cycle's differences and its Courant check (host only, no device work).
+pic_status fdtd_setup(pic_ctx* ctx);
+// Leapfrog step of the Yee fields with split B, in place (see fdtd.cu).
+pic_status fdtd_update(pic_ctx* ctx, double* const E[3], double* const B[3], const double* const J[3]);
+pic_status fdtd_update32(pic_ctx* ctx, float* const E[3], float* const B[3], const float* const J[3]);
+// nsteps of the hybrid FDTD cycle (FP64).
+pic_status fdtd_step(pic_ctx* ctx, double* const E[3], double* const B[3], double* const J[3], double* rho,
+                     const pic_species* sp, int n_species, int nsteps);
 
 // diag.cu ---------------------------------------------------------------------
 pic_status diag_energy(pic_ctx* ctx, const double* const E[3], const double* const B[3],

@@ -580,6 +580,8 @@ void gauss_legendre(GaussLegendre* g) {
 
 }  // namespace
 
+long double fornberg_alpha_s(int m, int n) { return alpha_s(m, n); }
+
 pic_status psatd_setup(pic_ctx* ctx) {
   int64_t Nmax = std::max(ctx->N[0], std::max(ctx->N[1], ctx->N[2]));
   std::vector<double> h(9 * Nmax, 0.0);
@@ -587,7 +589,9 @@ pic_status psatd_setup(pic_ctx* ctx) {
   for (int a = 0; a < 3; ++a) {
     const int64_t N = ctx->N[a];
     const double dx = ctx->dx[a];
-    const int ms = ctx->sorder[a] / 2, mc = ctx->corder[a] / 2;
+    // FDTD cycle: ks is the symbol of its finite difference (order 2 when the order is 0)
+    const int so = (ctx->cycle == PIC_CYCLE_HYBRID_FDTD && ctx->sorder[a] == 0) ? 2 : ctx->sorder[a];
+    const int ms = so / 2, mc = ctx->corder[a] / 2;
     for (int64_t j = 0; j < N; ++j) {
       const int64_t js = j < N / 2 ? j : j - N;  // signed index, Nyquist -> -N/2
       double ks, kc, zeta = 0.0;

@@ -16,7 +16,7 @@ from . import build as _build
 PIC_OK = 0
 PIC_FP64, PIC_FP32 = 0, 1
 PIC_PUSHER_BORIS, PIC_PUSHER_VAY = 0, 1
-PIC_CYCLE_HYBRID, PIC_CYCLE_NODAL, PIC_CYCLE_STAGGERED = 0, 1, 2
+PIC_CYCLE_HYBRID, PIC_CYCLE_NODAL, PIC_CYCLE_STAGGERED, PIC_CYCLE_HYBRID_FDTD = 0, 1, 2, 3
 STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_UNSUPPORTED", -3: "PIC_ERR_NOMEM",
           -4: "PIC_ERR_CUDA", -5: "PIC_ERR_CAPACITY", -6: "PIC_ERR_TIMEOUT", -7: "PIC_ERR_NONFINITE"}
 STANDARD, GALILEAN, AVERAGED = 0, 1, 2

@@ -46,7 +46,7 @@ def test_init_rejects_bad_extension_fields():
     from paper_2106_12919_gb300 import pic
     h = ctypes.c_void_p()
     L3, D3, I3 = ctypes.c_int64 * 3, ctypes.c_double * 3, ctypes.c_int32 * 3
-    for field, value in (("filter_passes", 9), ("filter_passes", -1), ("pusher", 2), ("cycle", 3), ("reserved", 1)):
+    for field, value in (("filter_passes", 9), ("filter_passes", -1), ("pusher", 2), ("cycle", 4), ("reserved", 1)):
         e = pic.PicExt()
         pic.LIB.pic_ext_default(ctypes.byref(e))
         setattr(e, field, value)
@@ -74,3 +74,32 @@ def test_init_rejects_bad_arguments_without_gpu_work():
         assert not h.value
     st = pic.LIB.pic_init(ctypes.byref(h), L3(16, 16, 16), D3(1, 1, 1), 1.0, 1, I3(8, 8, 8), 1, D3(0, 0, 1.5), None)
     assert st == -1                            # |v_gal| >= c
+
+
+def test_fdtd_cycle_validation_without_gpu_work():
+    """The FDTD cycle: unsupported options and a dt above its Courant limit are refused before
+    any device call."""
+    import ctypes
+    from paper_2106_12919_gb300 import pic
+    from oracle import fdtd
+    L3, D3, I3 = ctypes.c_int64 * 3, ctypes.c_double * 3, ctypes.c_int32 * 3
+
+    def init(dt, variant=0, dx=(1.0, 1.0, 1.0), orders=(0, 0, 0), **fields):
+        h = ctypes.c_void_p()
+        e = pic.PicExt()
+        pic.LIB.pic_ext_default(ctypes.byref(e))
+        e.cycle = pic.PIC_CYCLE_HYBRID_FDTD
+        e.spectral_order[:] = list(orders)
+        for k, v in fields.items():
+            setattr(e, k, v)
+        st = pic.LIB.pic_init(ctypes.byref(h), L3(16, 16, 16), D3(*dx), dt, 1, I3(8, 8, 8), variant,
+                              D3(0, 0, 0.5), ctypes.byref(e))
+        assert not h.value or st == 0
+        return st
+
+    assert init(0.5, variant=1) == -2                    # Galilean
+    assert init(0.5, filter_passes=1) == -2
+    assert init(0.5, precision=pic.PIC_FP32) == -2
+    for dx, orders in (((1.0, 1.0, 1.0), (0, 0, 0)), ((0.2, 0.2, 0.04), (4, 4, 8)), ((1.0, 0.5, 2.0), (2, 6, 4))):
+        lim = fdtd.courant_limit(tuple(o or 2 for o in orders), dx)
+        assert init(lim * 1.001, dx=dx, orders=orders) == -1, (dx, orders)

@@ -115,8 +115,9 @@ typedef enum {
  *     staggered difference sum_n c_n (f_{j+n} - f_{j-n+1}) / dx with c_n = alpha^s_{m,n} /
  *     (2n - 1), 2m = spectral_order of the axis (0 means 2: Yee's scheme), whose symbol is
  *     i [k]_s.  E, B are centered to the nodes and J to the Yee grid by the stencils of Sec. 3
- *     (Eq. staggered_finite_sum) in real space.  rho is deposited (rho^{n+1} on exit) but the
- *     solver does not use it.  Requires PIC_PSATD_STANDARD and filter_passes = 0
+ *     (Eq. staggered_finite_sum) in real space; filter_passes smooths the nodal J in real
+ *     space before its centering.  rho is deposited (rho^{n+1} on exit) but the solver does
+ *     not use it.  Both precisions (pic_step, pic_step32).  Requires PIC_PSATD_STANDARD
  *     (PIC_ERR_UNSUPPORTED otherwise) and dt within the Courant limit
  *     c dt sqrt(sum_a max_k [k_a]_s^2) <= 2 (PIC_ERR_ARG otherwise).  Default PIC_CYCLE_HYBRID.
  *   reserved: must be 0.

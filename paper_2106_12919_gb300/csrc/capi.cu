@@ -188,9 +188,8 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   if (e.filter_passes < 0 || e.filter_passes > 8) return fail(PIC_ERR_ARG, "filter_passes must be in [0, 8]");
   if (e.pusher != PIC_PUSHER_BORIS && e.pusher != PIC_PUSHER_VAY) return fail(PIC_ERR_ARG, "unknown pusher");
   if (e.cycle < PIC_CYCLE_HYBRID || e.cycle > PIC_CYCLE_HYBRID_FDTD) return fail(PIC_ERR_ARG, "unknown cycle");
-  if (e.cycle == PIC_CYCLE_HYBRID_FDTD &&
-      (psatd_variant != PIC_PSATD_STANDARD || e.filter_passes != 0 || e.precision != PIC_FP64))
-    return fail(PIC_ERR_UNSUPPORTED, "the FDTD cycle takes the standard variant, no filter, FP64");
+  if (e.cycle == PIC_CYCLE_HYBRID_FDTD && psatd_variant != PIC_PSATD_STANDARD)
+    return fail(PIC_ERR_UNSUPPORTED, "the FDTD cycle has the standard (non-Galilean) update only");
   if (e.reserved) return fail(PIC_ERR_ARG, "reserved fields must be 0");
   if (psatd_variant != PIC_PSATD_STANDARD) {
     if (!v_gal) return fail(PIC_ERR_ARG, "v_gal required");

@@ -191,9 +191,14 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   const int64_t nm = ctx->nmode, nc = ctx->ncell;
   const float* cE[3] = {E[0], E[1], E[2]};
   const float* cB[3] = {B[0], B[1], B[2]};
-  PIC_TRY32(load_fields32(ctx, cE, cB));
+  // FDTD cycle: the caller's Yee E, B are the state, advanced in place; no spectra
+  const bool fd = ctx->cycle == PIC_CYCLE_HYBRID_FDTD;
+  const float* yee[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
+  float* nodal6[6];
+  for (int c = 0; c < 6; ++c) nodal6[c] = nodal(ctx) + c * nc;
   int cur = 0;
-  {
+  if (!fd) {
+    PIC_TRY32(load_fields32(ctx, cE, cB));
     CRP6<float> rin;
     CP6<float2> rout;
     rin.p[0] = rho;
@@ -202,7 +207,11 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     PIC_TRY32(fft_r2c<float>(ctx, rin, rout, 1));
   }
   const bool stag = ctx->cycle == PIC_CYCLE_STAGGERED;
-  if (stag) {
+  if (fd) {
+    // E^n, B^n -> nodes in real space (work arrays: the nodal J buffer, free until the deposit)
+    StageScope t(ctx, STAGE_OTHER, 9);
+    PIC_TRY32(center_to_nodal_t<float>(ctx, yee, nodal6, Jn(ctx), Jn(ctx) + nc));
+  } else if (stag) {
     // staggered comparison cycle: the first gather reads the caller's Yee E, B as they are
     const float* src[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
     for (int c = 0; c < 6; ++c)
@@ -264,6 +273,25 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
       else
         PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
     }
+    if (fd) {
+      // J^{n+1/2}: optional smoothing, nodes -> Yee (work arrays: the nodal E, B, free after the
+      // push), leapfrog of E, B, then E^{n+1}, B^{n+1} -> nodes for the next gather
+      {
+        StageScope t(ctx, STAGE_OTHER, 3 + 9 * ctx->filter_passes);
+        for (int c = 0; c < 3 && ctx->filter_passes > 0; ++c)
+          PIC_TRY32(bilinear_filter_t<float>(ctx, Jnp[c], ctx->filter_passes, nodal(ctx), nodal(ctx) + nc));
+        const float* cJn[3] = {Jnp[0], Jnp[1], Jnp[2]};
+        PIC_TRY32(center_to_yee_t<float>(ctx, cJn, J, nodal(ctx), nodal(ctx) + nc));
+      }
+      const float* cJ[3] = {J[0], J[1], J[2]};
+      PIC_TRY32(fdtd_update32(ctx, E, B, cJ));
+      if (!last) {
+        StageScope t(ctx, STAGE_OTHER, 9);
+        PIC_TRY32(center_to_nodal_t<float>(ctx, yee, nodal6, Jn(ctx), Jn(ctx) + nc));
+      }
+      ++ctx->steps_done;
+      continue;
+    }
     CRP6<float> in;
     CP6<float2> out;
     for (int c = 0; c < 3; ++c) {
@@ -293,6 +321,7 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     if (!last) PIC_TRY32(g_to_nodal32(ctx));
     ++ctx->steps_done;
   }
+  if (fd) return PIC_OK;
   float* outs[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
   PIC_TRY32(store_yee32(ctx, EBh(ctx), kKindEB, 6, outs));
   float* jouts[3] = {J[0], J[1], J[2]};

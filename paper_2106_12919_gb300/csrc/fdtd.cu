@@ -208,8 +208,11 @@ pic_status fdtd_step(pic_ctx* ctx, double* const E[3], double* const B[3], doubl
       PIC_TRY(particles_push(ctx, En, Bn, &sp[q], Jn, rho));
     }
     {
-      // J^{n+1/2} nodes -> Yee (scratch: ctx->nodal, free after the push)
-      StageScope t(ctx, STAGE_OTHER, 3);
+      // J^{n+1/2}: optional smoothing (Sec. 2), nodes -> Yee (work arrays: ctx->nodal, free after
+      // the push)
+      StageScope t(ctx, STAGE_OTHER, 3 + 9 * ctx->filter_passes);
+      for (int c = 0; c < 3 && ctx->filter_passes > 0; ++c)
+        PIC_TRY(bilinear_filter_t<double>(ctx, Jn[c], ctx->filter_passes, ctx->nodal, ctx->nodal + nc));
       PIC_TRY(center_to_yee(ctx, cJn, J));
     }
     PIC_TRY(fdtd_update(ctx, E, B, cJ));

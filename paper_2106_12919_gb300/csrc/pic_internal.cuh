@@ -285,6 +285,14 @@ pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int for
 // center.cu -------------------------------------------------------------------
 pic_status center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);
 pic_status center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* const out[3]);
+// Either precision, with explicit work arrays w0, w1 (ncell elements each).
+template <class T>
+pic_status center_to_nodal_t(pic_ctx* ctx, const T* const F[6], T* const out[6], T* w0, T* w1);
+template <class T>
+pic_status center_to_yee_t(pic_ctx* ctx, const T* const Jn[3], T* const out[3], T* w0, T* w1);
+// `passes` passes of the bilinear (1/4, 1/2, 1/4) filter along x, y, z of f in place (Sec. 2).
+template <class T>
+pic_status bilinear_filter_t(pic_ctx* ctx, T* f, int passes, T* w0, T* w1);
 
 // fdtd.cu ---------------------------------------------------------------------
 // Weights of the FDTD cycle's differences and its Courant check (host only, no device work).

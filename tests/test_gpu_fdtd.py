@@ -15,13 +15,16 @@ pytestmark = pytest.mark.gpu
 
 FDTD = 3
 
-# (workload, generator args, steps, finite-difference order per axis; 0 = Yee's order 2)
+# (workload, generator args, steps, finite-difference order per axis (0 = Yee's order 2), options)
 CASES = [
-    ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 4, (0, 0, 0)),
-    ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 4, (4, 8, 2)),
-    ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, (0, 0, 0)),
-    ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, (4, 4, 16)),
-    ("seed_wave", dict(shape=(16, 16, 16), ppc=2), 3, (2, 2, 2)),
+    ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 4, (0, 0, 0), {}),
+    ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 4, (4, 8, 2), {}),
+    ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, (0, 0, 0), {}),
+    ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, (4, 4, 16), {}),
+    ("seed_wave", dict(shape=(16, 16, 16), ppc=2), 3, (2, 2, 2), {}),
+    # the bilinear smoothing of J (Sec. 2) and Vay's pusher around the FDTD solver
+    ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 4, (0, 0, 0), {"filter_passes": 2}),
+    ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 3, (4, 4, 8), {"filter_passes": 1, "pusher": 1}),
 ]
 
 
@@ -58,19 +61,19 @@ def test_maxwell_step_matches_yee_update(orders):
     assert field_rel_err(g(dJ), J) == 0.0
 
 
-@pytest.mark.parametrize("name,kw,nsteps,orders", CASES)
-def test_fdtd_cycle_matches_oracle(name, kw, nsteps, orders):
+@pytest.mark.parametrize("name,kw,nsteps,orders,opts", CASES)
+def test_fdtd_cycle_matches_oracle(name, kw, nsteps, orders, opts):
     import torch
     w = workloads.WORKLOADS[name](**kw)
     p = _params(w, orders)
     shape = p["shape"]
-    prm = step.Params(**p, cycle=FDTD)
+    prm = step.Params(**p, cycle=FDTD, **opts)
     st = {"E": [a.copy() for a in w["E"]], "B": [a.copy() for a in w["B"]],
           "species": [dict(s) for s in w["species"]]}
     st["rho"] = step.initial_rho(prm, st["species"])
     for _ in range(nsteps):
         step.hybrid_step(prm, st)
-    ctx = context_for(p, sort_interval=2, cycle=FDTD)
+    ctx = context_for(p, sort_interval=2, cycle=FDTD, **opts)
     E = [to_dev(a) for a in w["E"]]
     B = [to_dev(a) for a in w["B"]]
     J = [torch.empty(ctx.ncell, dtype=torch.float64, device="cuda") for _ in range(3)]

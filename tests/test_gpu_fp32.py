@@ -158,6 +158,9 @@ CASES = [
     # the nodal comparison cycle
     ("laser_wakefield:nodal", dict(shape=(16, 16, 64), ppc=1), 100, False),
     ("laser_wakefield:stag", dict(shape=(16, 16, 64), ppc=1), 100, False),
+    # the hybrid FDTD cycle: Yee's order 2; order (4, 4, 16) with the filter
+    ("laser_wakefield:fdtd", dict(shape=(16, 16, 64), ppc=1), 100, False),
+    ("laser_wakefield:fdtd_hi", dict(shape=(16, 16, 64), ppc=1), 100, False),
     # particles only in z < L/2: empty tiles and chunks in the other half of the box
     ("laser_wakefield:half", dict(shape=(16, 16, 64), ppc=2), 100, False),
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 100, True),
@@ -204,6 +207,12 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
     w = workloads.WORKLOADS[name](**kw)
     p = w["params"]
     shape, dx = p["shape"], p["dx"]
+    if opt.startswith("fdtd"):
+        from oracle import fdtd
+        p = dict(p)
+        p["spectral_order"] = (4, 4, 16) if opt == "fdtd_hi" else (0, 0, 0)
+        p["dt"] = 0.9 * fdtd.courant_limit(tuple(o or 2 for o in p["spectral_order"]), dx, p["c"])
+        opts = {"cycle": 3, "filter_passes": 1 if opt == "fdtd_hi" else 0}
     if opt == "half":
         half = 0.5 * shape[2] * dx[2]
         w["species"] = [{k: (v[s["z"] < half] if isinstance(v, np.ndarray) else v) for k, v in s.items()}

@@ -15,44 +15,44 @@ template <class T>
 struct StencilArgs {
   const T* in;
   T* out;
-  int64_t N[3];
-  int axis;
+  int ncell;
+  int shift, mask;  // the axis: index stride 2^shift, coordinate j = (e >> shift) & mask
   int mode;  // 0: nodal -> staggered, 1: staggered -> nodal, 2: bilinear (1/4, 1/2, 1/4) filter
   int m;
   T w[PIC_MAX_CENTER_M];
 };
 
+// One output element per thread; grids are powers of two (at most 2^30 cells), so the index
+// arithmetic is 32-bit shifts and masks.
 template <class T>
-__global__ void stencil_kernel(StencilArgs<T> a) {
-  const int64_t ncell = a.N[0] * a.N[1] * a.N[2];
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= ncell) return;
-  const int64_t iz = e % a.N[2], r = e / a.N[2];
-  const int64_t iy = r % a.N[1], ix = r / a.N[1];
-  const int64_t idx[3] = {ix, iy, iz};
-  const int64_t stride[3] = {a.N[1] * a.N[2], a.N[2], 1};
-  const int64_t N = a.N[a.axis], j = idx[a.axis], st = stride[a.axis];
-  const int64_t base = e - j * st;
-  const int64_t mask = N - 1;
+__global__ void __launch_bounds__(256) stencil_kernel(StencilArgs<T> a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.ncell) return;
+  const int j = (e >> a.shift) & a.mask;
+  const int base = e - (j << a.shift);
+  const T* in = a.in;
   if (a.mode == 2) {
     // f_j <- f_{j-1} / 4 + f_j / 2 + f_{j+1} / 4 (Sec. 2, the smoothing of the deposits)
-    a.out[e] = T(0.25) * a.in[base + ((j - 1) & mask) * st] + T(0.5) * a.in[e] +
-               T(0.25) * a.in[base + ((j + 1) & mask) * st];
+    a.out[e] = T(0.25) * in[base + (((j - 1) & a.mask) << a.shift)] + T(0.5) * in[e] +
+               T(0.25) * in[base + (((j + 1) & a.mask) << a.shift)];
     return;
   }
+  // mode 1: f_j = sum_n w_n (s[j+n-1] + s[j-n]); mode 0: f_{j+1/2} = sum_n w_n (g[j+n] + g[j-n+1])
+  const int d = a.mode == 1 ? -1 : 0;
   T acc = T(0);
-  for (int n = 1; n <= a.m; ++n) {
-    int64_t i1, i2;
-    if (a.mode == 1) {
-      i1 = (j + n - 1) & mask;
-      i2 = (j - n) & mask;
-    } else {
-      i1 = (j + n) & mask;
-      i2 = (j - n + 1) & mask;
-    }
-    acc += a.w[n - 1] * (a.in[base + i1 * st] + a.in[base + i2 * st]);
+#pragma unroll
+  for (int n = 1; n <= PIC_MAX_CENTER_M; ++n) {
+    if (n > a.m) break;
+    const int i1 = (j + n + d) & a.mask, i2 = (j - n + 1 + d) & a.mask;
+    acc += a.w[n - 1] * (in[base + (i1 << a.shift)] + in[base + (i2 << a.shift)]);
   }
   a.out[e] = acc;
+}
+
+int lg2i(int64_t n) {
+  int s = 0;
+  while ((int64_t(1) << s) < n) ++s;
+  return s;
 }
 
 template <class T>
@@ -61,8 +61,9 @@ pic_status run(pic_ctx* ctx, const T* in, T* out, int axis, int mode) {
   memset(&s, 0, sizeof(s));
   s.in = in;
   s.out = out;
-  for (int d = 0; d < 3; ++d) s.N[d] = ctx->N[d];
-  s.axis = axis;
+  s.ncell = (int)ctx->ncell;
+  s.shift = axis == 0 ? lg2i(ctx->N[1]) + lg2i(ctx->N[2]) : axis == 1 ? lg2i(ctx->N[2]) : 0;
+  s.mask = (int)ctx->N[axis] - 1;
   s.mode = mode;
   s.m = ctx->cw[axis].m;
   for (int n = 0; n < s.m; ++n) s.w[n] = (T)ctx->cw[axis].w[n];

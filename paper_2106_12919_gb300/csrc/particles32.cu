@@ -783,10 +783,7 @@ struct Key32Args {
   uint32_t* counts;
 };
 
-__global__ void key32_kernel(Key32Args a) {
-  if (gated_off(a.gate)) return;
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= a.n) return;
+__device__ __forceinline__ void key32_one(const Key32Args& a, int64_t p) {
   const int c = a.cell[p];
   const int cx = (c >> (a.shz + a.shy)) & a.mask[0], cy = (c >> a.shz) & a.mask[1], cz = c & a.mask[2];
   const int t = (int)(((cx >> a.tshift[0]) * a.nty + (cy >> a.tshift[1])) * a.ntz + (cz >> a.tshift[2]));
@@ -799,12 +796,17 @@ __global__ void key32_kernel(Key32Args a) {
   if ((int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + k, (uint32_t)__popc(peers));
 }
 
+__global__ void key32_kernel(Key32Args a) {
+  if (gated_off(a.gate)) return;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x)
+    key32_one(a, p);
+}
+
 // exclusive scan, phase 1: each block scans 4096 counts in place (to offsets within the block)
 // and writes its total to bsum[block]
-__global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n, uint32_t* bsum, const int* gate) {
-  if (gated_off(gate)) return;
-  __shared__ uint32_t part[1024];
-  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+__device__ __forceinline__ void scan_one_block(uint32_t* v, int64_t n, uint32_t* bsum, int64_t blk,
+                                               uint32_t* part) {
+  const int64_t base = blk * kScanBlock;
   uint32_t x[4];
   uint32_t s = 0;
 #pragma unroll
@@ -828,7 +830,17 @@ __global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n
     if (i < n) v[i] = run;
     run += x[q];
   }
-  if (threadIdx.x == 1023) bsum[blockIdx.x] = part[1023];
+  if (threadIdx.x == 1023) bsum[blk] = part[1023];
+}
+
+__global__ void __launch_bounds__(1024) scan_block_kernel(uint32_t* v, int64_t n, uint32_t* bsum, const int* gate) {
+  if (gated_off(gate)) return;
+  __shared__ uint32_t part[1024];
+  const int64_t nblk = (n + kScanBlock - 1) / kScanBlock;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    __syncthreads();  // part[] of the previous block is consumed
+    scan_one_block(v, n, bsum, blk, part);
+  }
 }
 
 // phase 2: one CTA scans the block totals (exclusive) and writes the grand total
@@ -861,13 +873,12 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* bsum, int64_t
 __global__ void scan_add_kernel(uint32_t* v, int64_t n, const uint32_t* bsum, int cpt_shift, int64_t* tile_off,
                                 int64_t n_tiles, const uint32_t* total, const int* gate) {
   if (gated_off(gate)) return;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t o = v[i] + bsum[i / kScanBlock];
     v[i] = o;
     if ((i & ((int64_t(1) << cpt_shift) - 1)) == 0) tile_off[i >> cpt_shift] = (int64_t)o;
   }
-  if (i == 0) tile_off[n_tiles] = (int64_t)*total;
+  if (blockIdx.x == 0 && threadIdx.x == 0) tile_off[n_tiles] = (int64_t)*total;
 }
 
 // map[k] = tile of chunk k, for the chunks [start[t], start[t + 1]) of every tile t
@@ -904,10 +915,15 @@ struct Scatter32Args {
   uint32_t* cursor;        // zeroed
 };
 
+__device__ __forceinline__ void scatter32_one(const Scatter32Args& a, int64_t p);
+
 __global__ void scatter32_kernel(Scatter32Args a) {
   if (gated_off(a.gate)) return;
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= a.n) return;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x)
+    scatter32_one(a, p);
+}
+
+__device__ __forceinline__ void scatter32_one(const Scatter32Args& a, int64_t p) {
   const int k = a.key[p];
   const unsigned active = __activemask();
   const unsigned peers = __match_any_sync(active, k);
@@ -944,8 +960,12 @@ __global__ void copy_back_kernel(CopyBackArgs a) {
 
 }  // namespace
 
+#ifndef PIC_BIN_LIMIT
+#define PIC_BIN_LIMIT 0.02
+#endif
+
 pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force) {
-  const unsigned long long limit = (unsigned long long)(0.02 * (double)total_particles);
+  const unsigned long long limit = (unsigned long long)(PIC_BIN_LIMIT * (double)total_particles);
   bin_decide_kernel<<<1, 1, 0, ctx->stream>>>(ctx->bin_gate, ctx->bin_outside, limit, force);
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
@@ -1032,18 +1052,21 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   b.cpt_shift = ilog2(ctx->tile[0]) + ilog2(ctx->tile[1]) + ilog2(ctx->tile[2]);
   b.key = ctx->bin_tid;
   b.counts = counts;
+  // grid-stride kernels on a capped grid: when the gate is off they return at once, so a gated
+  // binning costs a few microseconds, not a full-size launch
   const int bs = 256;
-  const unsigned nb = (unsigned)((n + bs - 1) / bs);
+  const unsigned nb = (unsigned)std::min<int64_t>((n + bs - 1) / bs, fill_blocks);
   if (n > 0) {
     key32_kernel<<<nb, bs, 0, ctx->stream>>>(b);
     PIC_LAUNCH_CHECK(ctx);
   }
-  scan_block_kernel<<<(unsigned)nblk, 1024, 0, ctx->stream>>>(counts, ncell, bsum, gate);
+  scan_block_kernel<<<(unsigned)std::min<int64_t>(nblk, 152 * 2), 1024, 0, ctx->stream>>>(counts, ncell, bsum, gate);
   PIC_LAUNCH_CHECK(ctx);
   scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(bsum, nblk, total, gate);
   PIC_LAUNCH_CHECK(ctx);
   int64_t* tile_off = offsets_out ? offsets_out : ctx->bin_counts;
-  scan_add_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, ctx->stream>>>(counts, ncell, bsum, b.cpt_shift,
+  scan_add_kernel<<<(unsigned)std::min<int64_t>((ncell + 255) / 256, fill_blocks), 256, 0, ctx->stream>>>(
+      counts, ncell, bsum, b.cpt_shift,
                                                                            tile_off, ctx->n_tiles, total, gate);
   PIC_LAUNCH_CHECK(ctx);
   if (chunks_out) {
@@ -1053,7 +1076,8 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
     uint32_t* ctotal = cbsum + nblk_t;
     chunk_count_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(tile_off, nt, chunks_out, gate);
     PIC_LAUNCH_CHECK(ctx);
-    scan_block_kernel<<<(unsigned)nblk_t, 1024, 0, ctx->stream>>>(chunks_out, nt, cbsum, gate);
+    scan_block_kernel<<<(unsigned)std::min<int64_t>(nblk_t, 152 * 2), 1024, 0, ctx->stream>>>(chunks_out, nt, cbsum,
+                                                                                            gate);
     PIC_LAUNCH_CHECK(ctx);
     scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(cbsum, nblk_t, ctotal, gate);
     PIC_LAUNCH_CHECK(ctx);

@@ -252,7 +252,6 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
         PIC_TRY32(particles_bin32_decide(ctx, total, force));
       }
       for (int q = 0; q < n_species && q < PIC_MAX_BINNED_SPECIES; ++q) {
-        StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 13 : 9);
         if (!ctx->sp_off[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
         if (!ctx->sp_chunk[q] || ctx->sp_chunk_n[q] < sp[q].n) {
           if (ctx->sp_chunk[q]) PIC_CUDA_TRY(ctx, cudaFree(ctx->sp_chunk[q]));
@@ -261,17 +260,25 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
           ctx->sp_chunk_n[q] = sp[q].n;
         }
         ctx->sp_off_n[q] = sp[q].n;
-        PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q]));
       }
     }
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(jn, 0, 3 * nc * sizeof(float), ctx->stream));
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(rho, 0, nc * sizeof(float), ctx->stream));
     for (int q = 0; q < n_species; ++q) {
-      StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
-      if (tiled && q < PIC_MAX_BINNED_SPECIES)
-        PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q], ctx->sp_chunk[q]));
-      else
+      if (tiled && q < PIC_MAX_BINNED_SPECIES) {
+        // the binning leaves the sorted species in the shared scratch and the push copies it back
+        // (so each species is binned right before its own push)
+        {
+          StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 12 : 9);
+          PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q], false));
+        }
+        StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
+        PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q], ctx->sp_chunk[q],
+                                         ctx->bin_gate));
+      } else {
+        StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
         PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
+      }
     }
     if (fd) {
       // J^{n+1/2}: optional smoothing, nodes -> Yee (work arrays: the nodal E, B, free after the

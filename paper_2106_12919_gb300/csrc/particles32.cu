@@ -31,6 +31,15 @@ struct Push32Args {
   float qw_scale;     // q / dV
   int gather;
   int vay;            // 1: Vay's pusher instead of Boris
+  // Tiled push only: when src_gate is set and *src_gate != 0 (the binning ran this step), the
+  // particles are read from the binning's sorted copy src[0..7] (cell, fx, fy, fz, ux, uy, uz, w
+  // as 32-bit words; id_src the ids or null) and written, with w and the ids, to the species
+  // arrays: the push is the copy back of the sort.
+  const int* src_gate;
+  const uint32_t* src[8];
+  const unsigned long long* id_src;
+  unsigned long long* id_dst;
+  float* w_dst;
 };
 
 // shape of order P from the base cell i and the offset f in [0, 1)
@@ -59,18 +68,18 @@ __device__ __forceinline__ void shape32(int i, float f, int& lo, float* S) {
   }
 }
 
-// u^{n-1/2} of particle p -> u^{n+1/2} with the gathered f = (E, B): Boris rotation, or Vay's pusher
-__device__ __forceinline__ void push_u(const Push32Args& a, int64_t p, const float* f, float& ux, float& uy,
-                                       float& uz) {
+// u^{n-1/2} = (u0x, u0y, u0z) -> u^{n+1/2} with the gathered f = (E, B): Boris rotation, or Vay's pusher
+__device__ __forceinline__ void push_u(const Push32Args& a, float u0x, float u0y, float u0z, const float* f,
+                                       float& ux, float& uy, float& uz) {
   const float kq = a.qm_half_dt;
   if (a.vay) {
-    ux = a.ux[p];
-    uy = a.uy[p];
-    uz = a.uz[p];
+    ux = u0x;
+    uy = u0y;
+    uz = u0z;
     vay_push<float>(ux, uy, uz, f, kq, a.inv_c2);
     return;
   }
-  const float umx = a.ux[p] + kq * f[0], umy = a.uy[p] + kq * f[1], umz = a.uz[p] + kq * f[2];
+  const float umx = u0x + kq * f[0], umy = u0y + kq * f[1], umz = u0z + kq * f[2];
   const float igm = rsqrtf(1.0f + (umx * umx + umy * umy + umz * umz) * a.inv_c2);
   const float tx = kq * f[3] * igm, ty = kq * f[4] * igm, tz = kq * f[5] * igm;
   const float s2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
   }
   // push u^{n-1/2} -> u^{n+1/2}
   float ux, uy, uz;
-  push_u(a, p, f, ux, uy, uz);
+  push_u(a, a.ux[p], a.uy[p], a.uz[p], f, ux, uy, uz);
   const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
   const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
   // displacement in cells
@@ -352,7 +361,7 @@ __global__ void __launch_bounds__(256) push32_stag_kernel(Push32Args a) {
     f[c] = gather32_one<P>(a.F[c], a, lo, (m & 1) ? S1[0] : S0[0], (m & 2) ? S1[1] : S0[1], (m & 4) ? S1[2] : S0[2]);
   }
   float ux, uy, uz;
-  push_u(a, p, f, ux, uy, uz);
+  push_u(a, a.ux[p], a.uy[p], a.uz[p], f, ux, uy, uz);
   const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
   const float v[3] = {ux * ig, uy * ig, uz * ig};
   int mc[3], nc[3];
@@ -479,13 +488,35 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   // Phase 1: gather, Boris push and move of every particle of the chunk; the new state goes to
   // memory.  Each thread sums |q w v_c| (c = x, y, z) and |q w| over its particles.
   float bnd[4] = {0.f, 0.f, 0.f, 0.f};
+  const bool sorted_src = a.src_gate != nullptr && *a.src_gate != 0;
   for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
     const int pr = interleaved(j, q, s);
     if (pr >= cnt) continue;
     const int p = p0 + pr;
-    const int c = a.cell[p];
+    int c;
+    float fx, fy, fz, u0x, u0y, u0z, wp;
+    if (sorted_src) {
+      c = (int)a.src[0][p];
+      fx = __uint_as_float(a.src[1][p]);
+      fy = __uint_as_float(a.src[2][p]);
+      fz = __uint_as_float(a.src[3][p]);
+      u0x = __uint_as_float(a.src[4][p]);
+      u0y = __uint_as_float(a.src[5][p]);
+      u0z = __uint_as_float(a.src[6][p]);
+      wp = __uint_as_float(a.src[7][p]);
+      a.w_dst[p] = wp;
+      if (a.id_src) a.id_dst[p] = a.id_src[p];
+    } else {
+      c = a.cell[p];
+      fx = a.fx[p];
+      fy = a.fy[p];
+      fz = a.fz[p];
+      u0x = a.ux[p];
+      u0y = a.uy[p];
+      u0z = a.uz[p];
+      wp = a.w[p];
+    }
     const int ix = (c >> (a.shz + a.shy)) & a.mask[0], iy = (c >> a.shz) & a.mask[1], iz = c & a.mask[2];
-    const float fx = a.fx[p], fy = a.fy[p], fz = a.fz[p];
     int lx, ly, lz;
     float Sx[NS], Sy[NS], Sz[NS];
     shape32<P>(ix, fx, lx, Sx);
@@ -533,7 +564,7 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
       }
     }
     float ux, uy, uz;
-    push_u(a, p, f, ux, uy, uz);
+    push_u(a, u0x, u0y, u0z, f, ux, uy, uz);
     const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
     const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
     const float dX = a.dtdx[0] * (vx - a.vg[0]), dY = a.dtdx[1] * (vy - a.vg[1]), dZ = a.dtdx[2] * (vz - a.vg[2]);
@@ -554,7 +585,7 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     a.ux[p] = ux;
     a.uy[p] = uy;
     a.uz[p] = uz;
-    const float qw = fabsf(a.w[p] * a.qw_scale);
+    const float qw = fabsf(wp * a.qw_scale);
     bnd[0] += qw * fabsf(vx);
     bnd[1] += qw * fabsf(vy);
     bnd[2] += qw * fabsf(vz);
@@ -669,6 +700,11 @@ Push32Args make_args32(pic_ctx* ctx, const pic_species32* sp) {
   a.inv_c2 = (float)(1.0 / (ctx->c * ctx->c));
   a.vay = ctx->pusher == PIC_PUSHER_VAY ? 1 : 0;
   a.qw_scale = (float)(sp->q / (ctx->dx[0] * ctx->dx[1] * ctx->dx[2]));
+  a.src_gate = nullptr;
+  for (int f = 0; f < 8; ++f) a.src[f] = nullptr;
+  a.id_src = nullptr;
+  a.id_dst = nullptr;
+  a.w_dst = nullptr;
   return a;
 }
 
@@ -996,7 +1032,7 @@ size_t tile_chunk_words(const pic_ctx* ctx, int64_t n) {
 
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                                   const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets,
-                                  const uint32_t* chunks) {
+                                  const uint32_t* chunks, const int* sorted_gate) {
   Push32Args a = make_args32(ctx, sp);
   for (int c = 0; c < 3; ++c) {
     a.F[c] = En[c];
@@ -1005,6 +1041,15 @@ pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const 
   }
   a.rho = rho;
   a.gather = 1;
+  if (sorted_gate) {
+    // the binning of this species (if the gate let it run) left its sorted copy in bin_tmp
+    const uint32_t* tmp = reinterpret_cast<const uint32_t*>(ctx->bin_tmp);
+    a.src_gate = sorted_gate;
+    for (int f = 0; f < 8; ++f) a.src[f] = tmp + (int64_t)f * ctx->bin_cap;
+    a.id_src = sp->id ? reinterpret_cast<const unsigned long long*>(ctx->bin_tmp + 4 * ctx->bin_cap) : nullptr;
+    a.id_dst = reinterpret_cast<unsigned long long*>(sp->id);
+    a.w_dst = sp->w;
+  }
   return launch_push32_tiled(ctx, a, offsets, chunks);
 }
 
@@ -1018,7 +1063,7 @@ pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float*
 }
 
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate,
-                           uint32_t* chunks_out) {
+                           uint32_t* chunks_out, bool copy_back) {
   const int64_t n = sp->n;
   pic_status st = particles_bin_capacity(ctx, n > 0 ? n : 1);
   if (st != PIC_OK) return st;
@@ -1106,6 +1151,7 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   s.cursor = ctx->cell_cursor;
   scatter32_kernel<<<nb, bs, 0, ctx->stream>>>(s);
   PIC_LAUNCH_CHECK(ctx);
+  if (!copy_back) return PIC_OK;  // the next tiled push reads the sorted copy
   CopyBackArgs cb;
   cb.gate = gate;
   for (int f = 0; f < 8; ++f) {

@@ -274,11 +274,15 @@ bool tiled_push_fits(const pic_ctx* ctx);  // deposit window of the tile fits in
 size_t tile_chunk_words(const pic_ctx* ctx, int64_t n);  // chunk list size for n particles (words)
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                                   const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets,
-                                  const uint32_t* chunks);
+                                  const uint32_t* chunks,
+                                  const int* sorted_gate = nullptr);
 // gate: device flag; the binning kernels do nothing while *gate == 0 (nullptr = always bin).
 // chunks_out (optional, tile_chunk_words entries): chunk starts for particles_push32_tiled.
+// copy_back = false leaves the sorted particles in ctx->bin_tmp (the species arrays untouched) for
+// a particles_push32_tiled call with sorted_gate = gate, which reads them there when the gate let
+// the binning run and writes the pushed particles to the species arrays.
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate = nullptr,
-                           uint32_t* chunks_out = nullptr);
+                           uint32_t* chunks_out = nullptr, bool copy_back = true);
 // *bin_gate = (particles whose new cell left their tile in the last tiled push > 2 % of total) || force
 pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force);
 

@@ -197,7 +197,8 @@ typedef struct {
 /*
  * pic_step: advance fields and particles by nsteps hybrid PIC steps (Sec. 2).
  *   E[3], B[3]  in/out: Yee-grid fields at t^n on entry, t^{n+nsteps} on exit.
- *   J[3]        out: J^{n+nsteps-1/2} on the Yee grid (centered from the nodal deposit).
+ *   J[3]        out: J^{n+nsteps-1/2} on the Yee grid (centered from the nodal deposit), or
+ *               J = NULL when the caller does not need it (saves the three transforms of J).
  *   rho         in/out: nodal rho^n on entry (see pic_deposit_rho), rho^{n+nsteps} on exit.
  *   sp          n_species species (positions x^n, momenta u^{n-1/2} on entry).
  * Per step: gather at x^n from the nodal E, B (Sec. 2); Boris push; move by

@@ -135,7 +135,7 @@ void pic_destroy(pic_ctx* ctx) {
   void* ptrs[] = {ctx->k1d, ctx->twid[0], ctx->twid[1], ctx->twid[2], ctx->coef, ctx->EBh,
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
                   ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work, ctx->bin_gate,
-                  ctx->bin_outside, ctx->flt1d};
+                  ctx->bin_outside, ctx->flt1d, ctx->bin_flags};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) {
@@ -418,12 +418,17 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
                     const pic_species* sp, int n_species, int nsteps) {
   if (!ctx) return PIC_ERR_ARG;
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
-  if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || !all_nonnull(J, 3) || !rho)
+  if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || (J && !all_nonnull(J, 3)) || !rho)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   if (nsteps < 0) return pic_set_error(ctx, PIC_ERR_ARG, "nsteps < 0");
   PIC_TRY(check_species(ctx, sp, n_species));
   if (nsteps == 0) return PIC_OK;
-  if (ctx->cycle == PIC_CYCLE_HYBRID_FDTD) return fdtd_step(ctx, E, B, J, rho, sp, n_species, nsteps);
+  if (ctx->cycle == PIC_CYCLE_HYBRID_FDTD) {
+    // the Yee J is a work array of the FDTD update: without the caller's, the spectral scratch
+    double* g = reinterpret_cast<double*>(ctx->G);
+    double* Jw[3] = {g, g + ctx->ncell, g + 2 * ctx->ncell};
+    return fdtd_step(ctx, E, B, J ? J : Jw, rho, sp, n_species, nsteps);
+  }
   const int64_t nm = ctx->nmode, nc = ctx->ncell;
   // entry: spectral E^n, B^n, rho^n; nodal gather fields
   const double* cE[3] = {E[0], E[1], E[2]};
@@ -490,8 +495,8 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
     {
       // hybrid: J nodal (centered in the update), G = nodal E, B; staggered: J and G on the Yee grid
       StageScope t(ctx, STAGE_UPDATE, 1);
-      PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], stag ? 1 : 0, stag ? 1 : 0, last ? 1 : 0,
-                              1));
+      PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], stag ? 1 : 0, stag ? 1 : 0,
+                              (last && J) ? 1 : 0, 1));
     }
     cur = 1 - cur;
     if (!last) PIC_TRY(g_to_nodal(ctx));
@@ -500,6 +505,7 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
   // exit: Yee E, B and J
   double* outs[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
   PIC_TRY(store_yee(ctx, ctx->EBh, kKindEB, 6, outs));
+  if (!J) return PIC_OK;
   double* jouts[3] = {J[0], J[1], J[2]};
   return store_yee(ctx, ctx->Jh, kKindJ, 3, jouts);
 }

@@ -183,7 +183,7 @@ pic_status pic_total_charge32(pic_ctx* ctx, const float* rho, double* out) {
 pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float* const J[3], float* rho,
                       const pic_species32* sp, int n_species, int nsteps) {
   PIC_NEED_FP32(ctx);
-  if (!nonnull(E, 3) || !nonnull(B, 3) || !nonnull(J, 3) || !rho)
+  if (!nonnull(E, 3) || !nonnull(B, 3) || (J && !nonnull(J, 3)) || !rho)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   if (nsteps < 0) return pic_set_error(ctx, PIC_ERR_ARG, "nsteps < 0");
   PIC_TRY32(check_species32(ctx, sp, n_species));
@@ -191,8 +191,12 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   const int64_t nm = ctx->nmode, nc = ctx->ncell;
   const float* cE[3] = {E[0], E[1], E[2]};
   const float* cB[3] = {B[0], B[1], B[2]};
-  // FDTD cycle: the caller's Yee E, B are the state, advanced in place; no spectra
+  // FDTD cycle: the caller's Yee E, B are the state, advanced in place; no spectra.  Its Yee J is a
+  // work array of the update: without the caller's, the spectral scratch.
   const bool fd = ctx->cycle == PIC_CYCLE_HYBRID_FDTD;
+  float* Jw[3] = {f1(reinterpret_cast<double*>(ctx->G)), f1(reinterpret_cast<double*>(ctx->G)) + nc,
+                  f1(reinterpret_cast<double*>(ctx->G)) + 2 * nc};
+  float* const* Jy = J ? J : Jw;
   const float* yee[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
   float* nodal6[6];
   for (int c = 0; c < 6; ++c) nodal6[c] = nodal(ctx) + c * nc;
@@ -274,7 +278,7 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
         }
         StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
         PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q], ctx->sp_chunk[q],
-                                         ctx->bin_gate));
+                                         bin32_scatter_gate(ctx)));
       } else {
         StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
         PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
@@ -288,9 +292,9 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
         for (int c = 0; c < 3 && ctx->filter_passes > 0; ++c)
           PIC_TRY32(bilinear_filter_t<float>(ctx, Jnp[c], ctx->filter_passes, nodal(ctx), nodal(ctx) + nc));
         const float* cJn[3] = {Jnp[0], Jnp[1], Jnp[2]};
-        PIC_TRY32(center_to_yee_t<float>(ctx, cJn, J, nodal(ctx), nodal(ctx) + nc));
+        PIC_TRY32(center_to_yee_t<float>(ctx, cJn, Jy, nodal(ctx), nodal(ctx) + nc));
       }
-      const float* cJ[3] = {J[0], J[1], J[2]};
+      const float* cJ[3] = {Jy[0], Jy[1], Jy[2]};
       PIC_TRY32(fdtd_update32(ctx, E, B, cJ));
       if (!last) {
         StageScope t(ctx, STAGE_OTHER, 9);
@@ -322,7 +326,7 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
       // hybrid: J nodal (centered in the update), G = nodal E, B; staggered: J and G on the Yee grid
       StageScope t(ctx, STAGE_UPDATE, 1);
       PIC_TRY32(psatd_update32(ctx, EBh(ctx), Jh(ctx), rhoh(ctx, cur), rhoh(ctx, 1 - cur), Gs(ctx), stag ? 1 : 0,
-                               stag ? 1 : 0, last ? 1 : 0, 1));
+                               stag ? 1 : 0, (last && J) ? 1 : 0, 1));
     }
     cur = 1 - cur;
     if (!last) PIC_TRY32(g_to_nodal32(ctx));
@@ -331,6 +335,7 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   if (fd) return PIC_OK;
   float* outs[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
   PIC_TRY32(store_yee32(ctx, EBh(ctx), kKindEB, 6, outs));
+  if (!J) return PIC_OK;
   float* jouts[3] = {J[0], J[1], J[2]};
   return store_yee32(ctx, Jh(ctx), kKindJ, 3, jouts);
 }

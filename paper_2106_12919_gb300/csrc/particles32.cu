@@ -798,6 +798,12 @@ __global__ void fill_u32_kernel(uint32_t* p, int64_t n, uint32_t v, const int* g
     p[e] = v;
 }
 
+// scatter gate = binning gate (1 without one) && the keys were out of order: an already sorted
+// species needs its tile ranges but no permutation
+__global__ void scatter_gate_kernel(const int* gate, const int* unsorted, int* sgate) {
+  *sgate = ((gate == nullptr || *gate != 0) && *unsorted != 0) ? 1 : 0;
+}
+
 // gate = (particles whose new cell left their tile in the last push) > limit, or forced; resets the count
 __global__ void bin_decide_kernel(int* gate, unsigned long long* outside, unsigned long long limit, int force) {
   *gate = (force || *outside > limit) ? 1 : 0;
@@ -817,16 +823,26 @@ struct Key32Args {
   int cpt_shift;           // log2 cells per tile
   int32_t* key;
   uint32_t* counts;
+  int* unsorted;           // set to 1 when some key is smaller than its predecessor's
 };
 
-__device__ __forceinline__ void key32_one(const Key32Args& a, int64_t p) {
-  const int c = a.cell[p];
+__device__ __forceinline__ int key_of(const Key32Args& a, int c) {
   const int cx = (c >> (a.shz + a.shy)) & a.mask[0], cy = (c >> a.shz) & a.mask[1], cz = c & a.mask[2];
   const int t = (int)(((cx >> a.tshift[0]) * a.nty + (cy >> a.tshift[1])) * a.ntz + (cz >> a.tshift[2]));
   const int local = ((((cy & a.tmask[1]) << a.lshift_x) | (cx & a.tmask[0])) << a.lshift_z) | (cz & a.tmask[2]);
-  const int k = (t << a.cpt_shift) | local;
+  return (t << a.cpt_shift) | local;
+}
+
+__device__ __forceinline__ void key32_one(const Key32Args& a, int64_t p) {
+  const int k = key_of(a, a.cell[p]);
   a.key[p] = k;
   const unsigned active = __activemask();
+  // already in key order?  (the lanes of a warp hold consecutive particles; lane 0 reads its
+  // predecessor's cell)
+  const int lane_id = threadIdx.x & 31;
+  const int up = __shfl_up_sync(active, k, 1);
+  const int prev = lane_id > 0 ? up : (p > 0 ? key_of(a, a.cell[p - 1]) : k);
+  if (prev > k) *a.unsorted = 1;
   const unsigned peers = __match_any_sync(active, k);
   const int leader = __ffs(peers) - 1;
   if ((int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + k, (uint32_t)__popc(peers));
@@ -1097,6 +1113,11 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   b.cpt_shift = ilog2(ctx->tile[0]) + ilog2(ctx->tile[1]) + ilog2(ctx->tile[2]);
   b.key = ctx->bin_tid;
   b.counts = counts;
+  if (!ctx->bin_flags) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_flags, 2 * sizeof(int)));
+  int* unsorted = ctx->bin_flags;
+  int* sgate = ctx->bin_flags + 1;
+  b.unsorted = unsorted;
+  PIC_CUDA_TRY(ctx, cudaMemsetAsync(unsorted, 0, sizeof(int), ctx->stream));
   // grid-stride kernels on a capped grid: when the gate is off they return at once, so a gated
   // binning costs a few microseconds, not a full-size launch
   const int bs = 256;
@@ -1131,12 +1152,17 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
     chunk_map_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(chunks_out, nt, chunks_out + chunk_map_offset(ctx), gate);
     PIC_LAUNCH_CHECK(ctx);
   }
-  if (n == 0) return PIC_OK;
+  if (n == 0) {
+    PIC_CUDA_TRY(ctx, cudaMemsetAsync(sgate, 0, sizeof(int), ctx->stream));
+    return PIC_OK;
+  }
+  scatter_gate_kernel<<<1, 1, 0, ctx->stream>>>(gate, unsorted, sgate);
+  PIC_LAUNCH_CHECK(ctx);
   if (!ctx->cell_cursor) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->cell_cursor, ncell * sizeof(uint32_t)));
-  fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(ctx->cell_cursor, ncell, 0u, gate);
+  fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(ctx->cell_cursor, ncell, 0u, sgate);
   PIC_LAUNCH_CHECK(ctx);
   Scatter32Args s;
-  s.gate = gate;
+  s.gate = sgate;
   void* fields[8] = {sp->cell, sp->fx, sp->fy, sp->fz, sp->ux, sp->uy, sp->uz, sp->w};
   uint32_t* tmp = reinterpret_cast<uint32_t*>(ctx->bin_tmp);
   for (int f = 0; f < 8; ++f) {
@@ -1153,7 +1179,7 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   PIC_LAUNCH_CHECK(ctx);
   if (!copy_back) return PIC_OK;  // the next tiled push reads the sorted copy
   CopyBackArgs cb;
-  cb.gate = gate;
+  cb.gate = sgate;
   for (int f = 0; f < 8; ++f) {
     cb.src[f] = s.dst[f];
     cb.dst[f] = static_cast<uint32_t*>(fields[f]);

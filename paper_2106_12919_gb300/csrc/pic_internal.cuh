@@ -127,6 +127,7 @@ struct pic_ctx {
   uint32_t* cell_cursor;  // FP32 binning: per-cell scatter cursors
   double* adj_work;       // reverse mode: rhobar^n, rhobar^{n+1}, 6 nodal force adjoints
   int* bin_gate;                    // FP32 form: device flag "re-bin before the next push"
+  int* bin_flags;                   // FP32 binning: [0] keys out of order, [1] scatter gate (see below)
   unsigned long long* bin_outside;  // FP32 form: particles whose new cell left their tile in the last push
 
   int64_t steps_done;
@@ -279,12 +280,15 @@ pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const 
 // gate: device flag; the binning kernels do nothing while *gate == 0 (nullptr = always bin).
 // chunks_out (optional, tile_chunk_words entries): chunk starts for particles_push32_tiled.
 // copy_back = false leaves the sorted particles in ctx->bin_tmp (the species arrays untouched) for
-// a particles_push32_tiled call with sorted_gate = gate, which reads them there when the gate let
-// the binning run and writes the pushed particles to the species arrays.
+// a particles_push32_tiled call with sorted_gate = bin32_scatter_gate(ctx), which reads them there
+// when the binning permuted them and writes the pushed particles to the species arrays.  A species
+// already in key order gets its tile ranges only (no permutation): the scatter gate stays 0.
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate = nullptr,
                            uint32_t* chunks_out = nullptr, bool copy_back = true);
 // *bin_gate = (particles whose new cell left their tile in the last tiled push > 2 % of total) || force
 pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force);
+// device flag: the last particles_bin32 call permuted the species (its sorted copy is in bin_tmp)
+inline const int* bin32_scatter_gate(const pic_ctx* ctx) { return ctx->bin_flags + 1; }
 
 // center.cu -------------------------------------------------------------------
 pic_status center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);

@@ -293,7 +293,8 @@ class Context:
     def step(self, E, B, J, rho, species, nsteps):
         """pic_step: E, B, J lists of 3 Yee arrays, rho nodal; species a list of Species."""
         n = self.ncell
-        self._check(LIB.pic_step(self.h, _parr(E, n), _parr(B, n), _parr(J, n), _ptr(rho, n),
+        self._check(LIB.pic_step(self.h, _parr(E, n), _parr(B, n), _parr(J, n) if J is not None else None,
+                                 _ptr(rho, n),
                                  _species_array(species), len(species), nsteps))
 
     def deposit_rho(self, species, rho):
@@ -358,7 +359,8 @@ class Context:
     # ---- FP32 form ----
     def step32(self, E, B, J, rho, species, nsteps):
         n = self.ncell
-        self._check(LIB.pic_step32(self.h, _parr(E, n), _parr(B, n), _parr(J, n), _ptr(rho, n),
+        self._check(LIB.pic_step32(self.h, _parr(E, n), _parr(B, n), _parr(J, n) if J is not None else None,
+                                   _ptr(rho, n),
                                    _species_array(species), len(species), nsteps))
 
     def deposit_rho32(self, species, rho):

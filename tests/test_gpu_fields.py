@@ -129,9 +129,24 @@ def test_field_energy_and_charge():
     Ed, Bd = [to_dev(a) for a in E], [to_dev(a) for a in B]
     W = ctx.field_energy(Ed, Bd)
     assert abs(W - diagnostics.field_energy(E, B, p["dx"])) < 1e-13 * W
-    lo, hi = (2, 1, 5), (9, 7, 30)
-    Wb = ctx.field_energy(Ed, Bd, lo, hi)
-    assert abs(Wb - diagnostics.field_energy(E, B, p["dx"], box_lo=lo, box_hi=hi)) < 1e-13 * Wb
+    # boxes: ragged z (scalar path), z a multiple of 4 (vector path), whole y-z planes (contiguous)
+    for lo, hi in (((2, 1, 5), (9, 7, 30)), ((3, 2, 4), (16, 5, 28)), ((5, 0, 0), (11, 8, 32))):
+        Wb = ctx.field_energy(Ed, Bd, lo, hi)
+        assert abs(Wb - diagnostics.field_energy(E, B, p["dx"], box_lo=lo, box_hi=hi)) < 1e-13 * Wb
+    # FP32 form: FP64 sums of the FP32 data
+    from paper_2106_12919_gb300 import pic
+    import torch
+    c32 = context_for(p, precision=pic.PIC_FP32)
+    E32 = [a.astype(np.float32) for a in E]
+    B32 = [a.astype(np.float32) for a in B]
+    d32 = lambda a: torch.from_numpy(a).cuda()
+    # values spread over twelve decades: the FP32 partial sums must carry the small terms
+    E32[0] *= np.exp(rng.uniform(-14, 14, size=shape)).astype(np.float32)
+    for lo, hi in ((None, None), ((2, 1, 5), (9, 7, 30)), ((5, 0, 0), (11, 8, 32))):
+        Wf = c32.field_energy32([d32(a) for a in E32], [d32(a) for a in B32], lo, hi)
+        ref = diagnostics.field_energy([a.astype(np.float64) for a in E32], [a.astype(np.float64) for a in B32],
+                                       p["dx"], box_lo=lo, box_hi=hi)
+        assert abs(Wf - ref) < 1e-13 * ref
     rho = rng.normal(size=shape)
     q = ctx.total_charge(to_dev(rho))
     assert abs(q - np.sum(rho) * np.prod(p["dx"])) < 1e-12 * np.sum(np.abs(rho))

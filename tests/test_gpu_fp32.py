@@ -137,6 +137,63 @@ def test_bin32_offsets_exact():
     assert np.all(np.diff(key[ids]) >= 0)
 
 
+def test_bin32_sorted_input_is_left_in_place():
+    """A second binning of an already binned species recomputes the tile ranges and leaves the
+    arrays bit for bit as they are (the permutation is skipped)."""
+    import torch
+    shape, dx, tile = (32, 16, 64), (0.5, 1.0, 0.25), (8, 8, 8)
+    p = dict(shape=shape, dx=dx, dt=0.1, shape_order=1, centering_order=(2, 2, 2), variant=0, v_gal=(0, 0, 0),
+             spectral_order=(0, 0, 0), c=1.0, eps0=1.0)
+    ctx = ctx32(p, tile=tile)
+    rng = np.random.default_rng(6)
+    n = 30000
+    sp = [{"x": rng.uniform(0, 16, n), "y": rng.uniform(0, 16, n), "z": rng.uniform(0, 16, n),
+           "ux": rng.normal(size=n), "uy": rng.normal(size=n), "uz": rng.normal(size=n), "w": rng.uniform(size=n),
+           "q": -1.0, "m": 1.0}]
+    (d,) = species32(sp, shape, dx)
+    off1 = torch.empty(ctx.num_tiles() + 1, dtype=torch.int64, device="cuda")
+    off2 = torch.empty_like(off1)
+    ctx.bin32(d, off1)
+    ctx.sync()
+    before = [to_host(a).copy() for a in d.arrays()]
+    ctx.bin32(d, off2)
+    ctx.sync()
+    np.testing.assert_array_equal(to_host(off2), to_host(off1))
+    for a, b in zip(before, [to_host(x) for x in d.arrays()]):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("cycle", [0, 3])
+def test_step32_without_J(cycle):
+    """J = NULL: the same fields, charge and particles as with J (the J transforms are skipped)."""
+    import torch
+    w = workloads.laser_wakefield(shape=(16, 16, 64), ppc=1)
+    p = dict(w["params"])
+    opts = {}
+    if cycle == 3:
+        from oracle import fdtd
+        p["dt"] = 0.9 * fdtd.courant_limit((2, 2, 2), p["dx"], p["c"])
+        opts = {"cycle": 3}
+    outs = []
+    for with_j in (True, False):
+        ctx = ctx32(p, sort_interval=10, **opts)
+        sp = species32(w["species"], p["shape"], p["dx"])
+        E = [dev32(a) for a in w["E"]]
+        B = [dev32(a) for a in w["B"]]
+        J = [torch.empty(ctx.ncell, dtype=torch.float32, device="cuda") for _ in range(3)] if with_j else None
+        rho = torch.empty(ctx.ncell, dtype=torch.float32, device="cuda")
+        ctx.deposit_rho32(sp, rho)
+        ctx.step32(E, B, J, rho, sp, 5)
+        ctx.sync()
+        (o,) = as_oracle_species(sp, p["shape"], p["dx"])
+        outs.append(([to_host(t).astype(np.float64) for t in E + B + [rho]], o))
+    (f1, s1), (f2, s2) = outs
+    assert field_rel_err(f2[:6], f1[:6]) < 1e-6
+    assert field_rel_err([f2[6]], [f1[6]]) < 1e-6
+    for k in ("ux", "uy", "uz"):
+        assert np.max(np.abs(s2[k] - s1[k])) <= 1e-6 * np.max(np.abs(s1[k]))
+
+
 # (workload, generator args, steps, chaotic): the laser- and beam-driven wakefield
 # families are the FP32 workloads of the target and are held to a flat 1e-5.  The
 # thermal plasma and the drifting pair plasma amplify any perturbation (thermal

@@ -126,3 +126,30 @@ def test_split_calls_equal_one_call():
         ctx.sync()
         outs.append([to_host(t) for t in E + B])
     assert field_rel_err(outs[1], outs[0]) < 1e-13
+
+
+@pytest.mark.parametrize("cycle", [0, 2, 3])
+def test_step_without_J(cycle):
+    """J = NULL: the same fields, charge and particles as with J (hybrid, staggered, FDTD)."""
+    import torch
+    w = workloads.thermal_plasma(shape=(16, 16, 16), ppc=2)
+    p = dict(w["params"])
+    if cycle == 3:
+        from oracle import fdtd
+        p["dt"] = 0.9 * fdtd.courant_limit((2, 2, 2), p["dx"], p["c"])
+    outs = []
+    for with_j in (True, False):
+        ctx = context_for(p, sort_interval=2, cycle=cycle)
+        E = [to_dev(a) for a in w["E"]]
+        B = [to_dev(a) for a in w["B"]]
+        J = [torch.empty(ctx.ncell, dtype=torch.float64, device="cuda") for _ in range(3)] if with_j else None
+        rho = torch.empty(ctx.ncell, dtype=torch.float64, device="cuda")
+        sp = species_to_dev(w["species"])
+        ctx.deposit_rho(sp, rho)
+        ctx.step(E, B, J, rho, sp, 3)
+        ctx.sync()
+        outs.append(([to_host(t) for t in E + B + [rho]], species_from_dev(sp)))
+    (f1, s1), (f2, s2) = outs
+    assert field_rel_err(f2, f1) < 1e-13
+    for k in ("x", "ux", "uz"):
+        assert np.max(np.abs(s2[0][k] - s1[0][k])) <= 1e-13 * max(1.0, np.max(np.abs(s1[0][k])))

@@ -41,6 +41,11 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 # the current kernel version at the full bench size
 # (profiles/push32_tile_laser_wakefield_128x128x512_dram.md); other workloads / forms report null
 MEASURED_TRAFFIC = {("laser_wakefield", (128, 128, 512), "fp32"): 1.490e9}
+# LSU data-pipe wavefronts (shared memory, L1, global) per steady-state launch of the same kernel,
+# same capture size (profiles/push32_tile_laser_wakefield_128x128x512_lsu.md): the pipe that bounds
+# the particle kernel on chip issues one wavefront per SM per cycle
+MEASURED_LSU_WAVEFRONTS = {("laser_wakefield", (128, 128, 512), "fp32"): 4.953e8}
+N_SM = 152
 # CPU-oracle sample: the same workload on a 1/64-volume box (same dx, dt, physics)
 SAMPLE_SHAPE = {"laser_wakefield": (32, 32, 128), "beam_wakefield": (64, 64, 128),
                 "thermal_plasma": (32, 32, 32), "galilean_drift": (32, 32, 64), "seed_wave": (32, 32, 32)}
@@ -418,6 +423,17 @@ def run_form(form, w, args, world, rank, local):
         roofline = {"kernel": "push32_tile_kernel (gather + Boris + deposit)", "bound": "hbm", "achieved": achieved,
                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                     "algorithmic_bytes": "60 B/particle + 40 B/cell per launch (%.3g B)" % nbytes}
+        wf = MEASURED_LSU_WAVEFRONTS.get((w["name"].rsplit("_", 1)[0], tuple(shape), form))
+        if wf is not None:
+            # the on-chip bound: the LSU data pipe (one wavefront per SM per cycle at the sampled clock)
+            mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+            peak_wf = N_SM * mhz * 1e6
+            roofline["onchip"] = {"bound": "lsu", "unit": "wavefronts/s", "achieved": wf / push_avg_s,
+                                  "peak": peak_wf, "frac": wf / push_avg_s / peak_wf,
+                                  "wavefronts_per_launch": wf,
+                                  "note": "LSU data-pipe wavefronts per launch from one ncu capture at this size; "
+                                          "peak = 152 SMs x 1 wavefront/cycle x median SM clock sampled in the "
+                                          "timed region"}
     else:
         flops = push_flops_per_particle(p["shape_order"]) * per_launch
         achieved = flops / push_avg_s / 1e12

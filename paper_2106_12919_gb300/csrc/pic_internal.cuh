@@ -44,6 +44,7 @@ template <> struct Cplx<double> { using type = double2; };
 template <> struct Cplx<float> { using type = float2; };
 __host__ __device__ __forceinline__ double2 to_c(double2 v, double2*) { return v; }
 __host__ __device__ __forceinline__ float2 to_c(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
+__host__ __device__ __forceinline__ float2 to_c(float2 v, float2*) { return v; }
 template <class C> __host__ __device__ __forceinline__ C cast_c(double2 v) { return to_c(v, (C*)nullptr); }
 template <class C> __host__ __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
 
@@ -100,6 +101,8 @@ struct pic_ctx {
   double* zeta[3];
   double* flt1d;     // [3][Nmax] bilinear filter symbols, (cos^2(k dx / 2))^passes; NULL when off
   double* flt[3];
+  float* k1d32;      // FP32 copies: [9][Nmax] as k1d, then [3][Nmax] half-cell shifts (re, im)
+  float* flt32;      // FP32 copy of flt1d
   double2* twid[3];  // twiddles exp(-2 pi i j / N_a), j < N_a
   float2* twid32[3]; // the same rounded to FP32
   double2* coef;     // [ncoef][nmode]

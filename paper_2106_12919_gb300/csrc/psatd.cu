@@ -256,10 +256,13 @@ struct UpdArgs {
   const C* rp;          // rho^{n+1}
   const double2* coef;  // [ncoef][nmode], FP64 in every form
   C* G;                 // [6][nmode] out
-  const double* ks[3];
-  const double* zt[3];
-  const double* flt[3];  // bilinear filter symbols per axis (NULL: no filter)
-  const double2* hs[3];  // half-cell shifts exp(-i k dx / 2)
+  // 1D tables in the data precision (the FP32 form reads FP32 copies of them: converting FP64
+  // values per mode would run on this part's slow FP64 pipe)
+  using R = decltype(C().x);
+  const R* ks[3];
+  const R* zt[3];
+  const R* flt[3];  // bilinear filter symbols per axis (NULL: no filter)
+  const C* hs[3];   // half-cell shifts exp(-i k dx / 2)
   int64_t Ny, nzh, nmode;
   double c2;
   double gscale;
@@ -364,8 +367,7 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
     u.G[4 * nm + m] = cscale(Gb[1], zx * zz * s);
     u.G[5 * nm + m] = cscale(Gb[2], zx * zy * s);
   } else {
-    const C hx = cconj(cast_c<C>(u.hs[0][ix])), hy = cconj(cast_c<C>(u.hs[1][iy])),
-            hz = cconj(cast_c<C>(u.hs[2][iz]));
+    const C hx = cconj(u.hs[0][ix]), hy = cconj(u.hs[1][iy]), hz = cconj(u.hs[2][iz]);
     u.G[0 * nm + m] = cscale(cmul(Ga[0], hx), s);
     u.G[1 * nm + m] = cscale(cmul(Ga[1], hy), s);
     u.G[2 * nm + m] = cscale(cmul(Ga[2], hz), s);
@@ -472,13 +474,13 @@ struct PhaseArgs {
   int mask[6];
   int sign;
   double scale;
-  const double2* hs[3];
+  const C* hs[3];  // half-cell shifts in the data precision
   int64_t Ny, nzh, nmode;
 };
 
-// The phase factors are formed in the data precision from the FP64 1D tables (GB300's FP64 rate is
-// a small fraction of its FP32 rate; in the FP32 form a product of up to three unit phases in FP32
-// is accurate to a few 1e-7, far below the transforms' own rounding).
+// The phase factors are formed in the data precision from 1D tables in that precision (GB300's FP64
+// rate is a small fraction of its FP32 rate; in the FP32 form a product of up to three unit phases
+// in FP32 is accurate to a few 1e-7, far below the transforms' own rounding).
 template <class C>
 __global__ void phase_kernel(PhaseArgs<C> p) {
   using T = decltype(C().x);
@@ -491,9 +493,9 @@ __global__ void phase_kernel(PhaseArgs<C> p) {
   f.x = (T)p.scale;
   f.y = (T)0;
   const int mk = p.mask[c];
-  if (mk & 1) f = cmul(f, cast_c<C>(p.hs[0][ix]));
-  if (mk & 2) f = cmul(f, cast_c<C>(p.hs[1][iy]));
-  if (mk & 4) f = cmul(f, cast_c<C>(p.hs[2][iz]));
+  if (mk & 1) f = cmul(f, p.hs[0][ix]);
+  if (mk & 2) f = cmul(f, p.hs[1][iy]);
+  if (mk & 4) f = cmul(f, p.hs[2][iz]);
   if (p.sign > 0) f.y = -f.y;
   p.out.p[c][m] = cmul(p.in.p[c][m], f);
 }
@@ -502,7 +504,7 @@ template <class C>
 struct NodalArgs {
   const C* EB;
   C* G;
-  const double* zt[3];
+  const decltype(C().x)* zt[3];  // centering symbols in the data precision
   int64_t Ny, nzh, nmode;
   double scale;
 };
@@ -646,6 +648,17 @@ pic_status psatd_setup(pic_ctx* ctx) {
     ctx->kc[a] = ctx->k1d + (3 + a) * Nmax;
     ctx->zeta[a] = ctx->k1d + (6 + a) * Nmax;
   }
+  {
+    // FP32 copies of the same 1D tables (same layout), rounded once here
+    std::vector<float> h32(9 * Nmax + 6 * Nmax);
+    for (int64_t i = 0; i < 9 * Nmax; ++i) h32[i] = (float)h[i];
+    for (int64_t i = 0; i < 3 * Nmax; ++i) {
+      h32[9 * Nmax + 2 * i] = (float)hs[i].x;
+      h32[9 * Nmax + 2 * i + 1] = (float)hs[i].y;
+    }
+    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->k1d32, h32.size() * sizeof(float)));
+    PIC_CUDA_TRY(ctx, cudaMemcpy(ctx->k1d32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   // bilinear filter symbols (Sec. 2): per pass and axis, (1/4, 1/2, 1/4) -> cos^2(k dx / 2)
   if (ctx->filter_passes > 0) {
     std::vector<double> hf(3 * Nmax, 0.0);
@@ -663,6 +676,9 @@ pic_status psatd_setup(pic_ctx* ctx) {
     PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->flt1d, 3 * Nmax * sizeof(double)));
     PIC_CUDA_TRY(ctx, cudaMemcpy(ctx->flt1d, hf.data(), 3 * Nmax * sizeof(double), cudaMemcpyHostToDevice));
     for (int a = 0; a < 3; ++a) ctx->flt[a] = ctx->flt1d + a * Nmax;
+    std::vector<float> hf32(hf.begin(), hf.end());
+    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->flt32, 3 * Nmax * sizeof(float)));
+    PIC_CUDA_TRY(ctx, cudaMemcpy(ctx->flt32, hf32.data(), 3 * Nmax * sizeof(float), cudaMemcpyHostToDevice));
   }
   // keep the half-cell shift tables right after the 1D tables
   ctx->ncoef = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN ? COEF_COUNT : COEF_PSI1;
@@ -695,6 +711,23 @@ static const double2* half_shift(const pic_ctx* ctx, int a) {
   return reinterpret_cast<const double2*>(ctx->k1d + 9 * Nmax) + a * Nmax;
 }
 
+// 1D tables of axis a ([k]_s, zeta, filter symbols or NULL, half-cell shifts) in FP64 or FP32
+static void tab1d(const pic_ctx* ctx, int a, const double** ks, const double** zt, const double** flt,
+                  const double2** hs) {
+  *ks = ctx->ks[a];
+  *zt = ctx->zeta[a];
+  *flt = ctx->filter_passes > 0 ? ctx->flt[a] : nullptr;
+  *hs = half_shift(ctx, a);
+}
+static void tab1d(const pic_ctx* ctx, int a, const float** ks, const float** zt, const float** flt,
+                  const float2** hs) {
+  const int64_t Nmax = std::max(ctx->N[0], std::max(ctx->N[1], ctx->N[2]));
+  *ks = ctx->k1d32 + (0 + a) * Nmax;
+  *zt = ctx->k1d32 + (6 + a) * Nmax;
+  *flt = ctx->filter_passes > 0 ? ctx->flt32 + a * Nmax : nullptr;
+  *hs = reinterpret_cast<const float2*>(ctx->k1d32 + 9 * Nmax) + a * Nmax;
+}
+
 template <class C>
 pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C* G, int g_mode, int j_yee,
                           int write_j, int smooth) {
@@ -706,10 +739,8 @@ pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C
   u.coef = ctx->coef;
   u.G = G;
   for (int a = 0; a < 3; ++a) {
-    u.ks[a] = ctx->ks[a];
-    u.zt[a] = ctx->zeta[a];
-    u.flt[a] = (smooth && ctx->filter_passes > 0) ? ctx->flt[a] : nullptr;
-    u.hs[a] = half_shift(ctx, a);
+    tab1d(ctx, a, &u.ks[a], &u.zt[a], &u.flt[a], &u.hs[a]);
+    if (!(smooth && ctx->filter_passes > 0)) u.flt[a] = nullptr;
   }
   u.Ny = ctx->N[1];
   u.nzh = ctx->nzh;
@@ -752,7 +783,12 @@ pic_status psatd_phase_t(pic_ctx* ctx, CP6<C> in, CP6<C> out, const int* comp_ki
   for (int c = 0; c < ncomp; ++c) p.mask[c] = stag_mask(comp_kind[c]);
   p.sign = sign;
   p.scale = scale;
-  for (int a = 0; a < 3; ++a) p.hs[a] = half_shift(ctx, a);
+  for (int a = 0; a < 3; ++a) {
+    const C* h;
+    const decltype(C().x)* unused[3];
+    tab1d(ctx, a, &unused[0], &unused[1], &unused[2], &h);
+    p.hs[a] = h;
+  }
   p.Ny = ctx->N[1];
   p.nzh = ctx->nzh;
   p.nmode = ctx->nmode;
@@ -778,7 +814,11 @@ pic_status psatd_to_nodal_t(pic_ctx* ctx, const C* EB6, C* G, double scale) {
   NodalArgs<C> a;
   a.EB = EB6;
   a.G = G;
-  for (int k = 0; k < 3; ++k) a.zt[k] = ctx->zeta[k];
+  for (int k = 0; k < 3; ++k) {
+    const decltype(C().x)* unused[2];
+    const C* h;
+    tab1d(ctx, k, &unused[0], &a.zt[k], &unused[1], &h);
+  }
   a.Ny = ctx->N[1];
   a.nzh = ctx->nzh;
   a.nmode = ctx->nmode;

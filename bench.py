@@ -156,7 +156,7 @@ def run_oracle_sample(name, steps):
     dt = time.perf_counter() - t0
     desc = "%d step(s) of the oracle on a %dx%dx%d sample of the workload (%d particles, same dx/dt/physics)" % (
         (steps,) + tuple(SAMPLE_SHAPE[name]) + (npart,))
-    return npart * steps / dt, desc, dt
+    return npart * steps / dt, desc, dt, w["params"], npart
 
 
 def reference_arm(args):
@@ -166,12 +166,19 @@ def reference_arm(args):
     steps_total = args.warmup + args.steps
     # warm-up samples are run too (untimed) so that the timed steps see warm caches
     run_oracle_sample(args.workload, max(1, min(args.warmup, 1)))
-    value, desc, secs = run_oracle_sample(args.workload, args.steps)
+    value, desc, secs, prm, n_sample = run_oracle_sample(args.workload, args.steps)
+    # the libpic arm's config: the full workload (the oracle times a bounded sample of it)
+    shape = tuple(args.grid) if args.grid else FULL_SHAPE[args.workload]
+    scale = float(np.prod(shape)) / float(np.prod(SAMPLE_SHAPE[args.workload]))
+    config = {"workload": args.workload, "grid": list(shape), "particles": int(round(n_sample * scale)),
+              "form": "fp64" if args.form == "fp64" else "fp32", "shape_order": prm["shape_order"],
+              "centering_order": list(prm["centering_order"]), "variant": prm["variant"],
+              "parallelism": "replicas" if args.gpus > 1 else "single"}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "form": "fp64", "sample": desc},
+        "data": "synthetic", "config": config,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -251,7 +258,7 @@ def main():
     line["roofline"]["peak_note"] = "HBM %.0f GB/s %s; FP64 peak derived: 152 SMs x 4 flop/clk x 2.07 GHz" % (
         hbm, "of measured" if peaks else "of fallback")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, _ = run_oracle_sample(args.workload, 4)
+        v, desc, _, _, _ = run_oracle_sample(args.workload, 4)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line), flush=True)

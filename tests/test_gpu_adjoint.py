@@ -69,9 +69,10 @@ def _probe_run(shape, ppc, steps, K, amplitude=0.01, order=1):
     return w, run, sp, profile, E0, B0
 
 
-def _forward_cells(run, sp, E0, B0, A, profile, du=None):
+def _forward_cells(run, sp, E0, B0, A, profile, du=None, margins=False):
     """Probe loss of one forward run and the cell index of every particle at every step
-    (state positions and the midpoints that carry the J deposit)."""
+    (state positions and the midpoints that carry the J deposit); with margins=True also each
+    particle's smallest distance (in cells) to a cell face over those positions."""
     import torch
     from paper_2106_12919_gb300 import pic
     ctx = run.ctx
@@ -89,6 +90,7 @@ def _forward_cells(run, sp, E0, B0, A, profile, du=None):
     dx = run.dx
     L = [ctx.shape[a] * dx[a] for a in range(3)]
     cells = []
+    near = torch.full_like(s.x, 1.0)
     for _ in range(run.nsteps):
         x0 = [s.x.clone(), s.y.clone(), s.z.clone()]
         J = [torch.empty_like(rho) for _ in range(3)]
@@ -99,36 +101,57 @@ def _forward_cells(run, sp, E0, B0, A, profile, du=None):
             mid = torch.remainder(x0[a] + 0.5 * d, L[a])
             cells.append(torch.floor(x1[a] / dx[a]).to(torch.int32))
             cells.append(torch.floor(mid / dx[a]).to(torch.int32))
+            if margins:
+                for v in (x1[a] / dx[a], mid / dx[a]):
+                    f = v - torch.floor(v)
+                    near = torch.minimum(near, torch.minimum(f, 1.0 - f))
+    if margins:
+        return ctx.field_energy(E, B, run.lo, run.hi), cells, near
     return ctx.field_energy(E, B, run.lo, run.hi), cells
 
 
-def _fd(run, sp, E0, B0, A, profile, grad, eps, du=None):
-    """Central difference with the smallest tried eps whose +/- runs cross no cell face."""
+def _fd(run, sp, E0, B0, A, profile, grad, eps, du=None, repeats=4, kinks=True):
+    """Central difference with the smallest tried eps whose +/- runs cross no cell face.
+
+    The FP64 deposits are atomic, so their summation order (and the loss, at ~1e-16 of it per
+    step, amplified by the plasma) varies from run to run; the difference is averaged over
+    `repeats` independent +/- pairs and returned with its standard error."""
     for _ in range(6):
         dp = None if du is None else [eps * d for d in du]
         dm = None if du is None else [-eps * d for d in du]
-        Lp, cp = _forward_cells(run, sp, E0, B0, A + (0 if du is not None else eps), profile, dp)
-        Lm, cm = _forward_cells(run, sp, E0, B0, A - (0 if du is not None else eps), profile, dm)
-        crossings = sum(int((a != b).sum()) for a, b in zip(cp, cm))
-        if crossings == 0:
-            return (Lp - Lm) / (2 * eps), eps
+        vals = []
+        for _ in range(repeats):
+            Lp, cp = _forward_cells(run, sp, E0, B0, A + (0 if du is not None else eps), profile, dp)
+            Lm, cm = _forward_cells(run, sp, E0, B0, A - (0 if du is not None else eps), profile, dm)
+            if kinks and sum(int((a != b).sum()) for a, b in zip(cp, cm)):
+                break
+            vals.append((Lp - Lm) / (2 * eps))
+        if len(vals) == repeats:
+            v = np.array(vals)
+            return float(v.mean()), eps, float(v.std(ddof=1) / np.sqrt(repeats))
         eps /= 10.0
     raise AssertionError("no crossing-free finite-difference step found")
 
 
-@pytest.mark.parametrize("shape,ppc,steps,K,order", [((32, 32, 32), 2, 12, 5, 3), ((32, 32, 32), 2, 12, 5, 1),
-                                                     ((64, 64, 64), 4, 12, 5, 1),
-                                                     ((64, 64, 64), 4, 50, 10, 1)])
-def test_gradient_matches_central_differences(shape, ppc, steps, K, order):
-    """eps = 1e-6 relative to the parameter (A, or |u0| for unit directions in momentum space),
-    reduced by tens while a +/- run crosses a cell face (the CIC shape is only piecewise
-    linear).  On the 32^3 / 12-step grids the bound is 1e-6 relative (plus the measured
-    run-to-run noise of the FP64 atomic deposits, negligible there).  On the full 64^3 /
-    50-step probe workload, avoiding every CIC kink forces eps down to ~1e-8, where the
-    run-to-run noise of the atomic deposits (their summation order varies, and 50 steps of
-    a thermal plasma amplify it to ~1e-12 of the loss) dominates the difference: that case
-    is held to 1e-3 and its numbers are printed; its 1e-6 check is the 32^3 cases plus the
-    1e-10 agreement with the oracle's own reverse pass."""
+@pytest.mark.parametrize("shape,ppc,steps,K,order,bound", [
+    ((32, 32, 32), 2, 12, 5, 3, None), ((32, 32, 32), 2, 12, 5, 1, None),
+    # the full probe grid and particle count (64^3, 1M particles): cubic (C2, no kinks) at 1e-6;
+    # CIC, whose kinks force eps towards the rounding of the loss, at the bound it can resolve
+    ((64, 64, 64), 4, 12, 5, 3, None), ((64, 64, 64), 4, 50, 10, 3, None),
+    ((64, 64, 64), 4, 12, 5, 1, 1e-4), ((64, 64, 64), 4, 50, 10, 1, 1e-3)])
+def test_gradient_matches_central_differences(shape, ppc, steps, K, order, bound):
+    """Central differences with eps = 1e-6 relative to the parameter (A, or |u0| for unit
+    directions in momentum space), each the mean of four independent +/- pairs: the FP64
+    deposits are atomic and their summation order varies from run to run, so the bound is
+    1e-6 relative plus four standard errors of that mean (a momentum direction's error relative
+    to the larger of its derivative and the typical one, ||g|| / sqrt(3n)).  The cubic shape is C2 and eps stays
+    at 1e-6.  The CIC shape is only piecewise linear: eps is reduced by tens while a +/- run
+    crosses a cell face, and momentum directions are drawn on the particles that stay 1e-4 cells
+    away from every face (the field response still moves the others).  On 32^3 that keeps 1e-6;
+    with the full 1M particles crossings drive eps to 1e-7..1e-9, where the difference of the two
+    losses nears their rounding and a thermal plasma's amplified deposit noise (~1e-12 of the
+    loss after 50 steps): those CIC cases are held to 1e-4 (12 steps) and 1e-3 (50 steps), and
+    the 1e-10 agreement with the oracle's own reverse pass checks the CIC adjoint exactly."""
     import torch
     from paper_2106_12919_gb300 import adjoint as gadj
     amp = 0.01
@@ -143,25 +166,37 @@ def test_gradient_matches_central_differences(shape, ppc, steps, K, order):
     loss.backward()
     gA = float(A.grad)
     gu = [ux.grad, uy.grad, uz.grad]
-    Ls = [_forward_cells(run, sp, E0, B0, amp, profile)[0] for _ in range(3)]
-    noise = max(Ls) - min(Ls) + 1e-16 * abs(Ls[0])
-    fdA, epsA = _fd(run, sp, E0, B0, amp, profile, gA, 1e-6 * amp)
-    full = shape[0] == 64 and steps == 50
-    tolA = 1e-3 if full else 1e-6 + 3 * noise / (2 * epsA * abs(fdA))
-    print("\ndL/dA adjoint %.12e  FD %.12e (eps %.1e)  rel %.2e  bound %.1e" %
-          (gA, fdA, epsA, abs(gA - fdA) / abs(fdA), tolA))
+    kinks = order == 1
+    fdA, epsA, seA = _fd(run, sp, E0, B0, amp, profile, gA, 1e-6 * amp, kinks=kinks)
+    # 1e-6 plus four standard errors of the averaged difference (the run-to-run noise)
+    tolA = bound if bound else 1e-6 + 4 * seA / abs(fdA)
+    print("\ndL/dA adjoint %.12e  FD %.12e (eps %.1e, s.e. %.1e)  rel %.2e  bound %.1e" %
+          (gA, fdA, epsA, seA / abs(fdA), abs(gA - fdA) / abs(fdA), tolA))
     assert abs(gA - fdA) < tolA * abs(fdA)
     g = torch.Generator(device="cuda").manual_seed(7)
     n = sp.n
     unorm = float(torch.sqrt(torch.sum(sp.ux ** 2 + sp.uy ** 2 + sp.uz ** 2)))
+    # momentum directions on the particles that stay 1e-4 cells from every face along the run:
+    # a relative eps of 1e-6 moves a trajectory by ~1e-6 cells, so the +/- runs cross no face
+    # and the difference keeps ~10 digits above the rounding of the loss
+    _, _, near = _forward_cells(run, sp, E0, B0, amp, profile, margins=True)
+    keep = (near > 1e-4).to(torch.float64)
+    print("momentum directions on %.1f%% of the particles" % (100.0 * float(keep.mean())))
+    # the typical size of g . d for a random unit d on that support: ||g|| / sqrt(components)
+    gnorm = float(torch.sqrt(sum(torch.sum((gu[a] * keep) ** 2) for a in range(3))))
+    typical = gnorm / np.sqrt(3.0 * float(keep.sum()))
     for trial in range(8 if shape[0] == 64 else 3):
-        d = torch.randn(3, n, dtype=torch.float64, device="cuda", generator=g)
+        d = torch.randn(3, n, dtype=torch.float64, device="cuda", generator=g) * keep
         d /= torch.linalg.norm(d)
         ad = float(sum(torch.dot(gu[a], d[a]) for a in range(3)))
-        fd, eps = _fd(run, sp, E0, B0, amp, profile, ad, 1e-6 * unorm, du=[d[0], d[1], d[2]])
-        tol = 1e-3 if full else 1e-6 + 3 * noise / (2 * eps * abs(fd))
-        rel = abs(ad - fd) / abs(fd)
-        print("direction %d: adjoint %.12e  FD %.12e (eps %.1e)  rel %.2e  bound %.1e" % (trial, ad, fd, eps, rel, tol))
+        fd, eps, se = _fd(run, sp, E0, B0, amp, profile, ad, 1e-6 * unorm, du=[d[0], d[1], d[2]], kinks=kinks)
+        # relative to the larger of |fd| and the typical directional derivative, so that a
+        # direction nearly orthogonal to the gradient does not turn rounding into a relative error
+        scale = max(abs(fd), typical)
+        tol = bound if bound else 1e-6 + 4 * se / scale
+        rel = abs(ad - fd) / scale
+        print("direction %d: adjoint %.12e  FD %.12e (eps %.1e, s.e. %.1e)  rel %.2e  bound %.1e" %
+              (trial, ad, fd, eps, se / abs(fd), rel, tol))
         assert rel < tol
 
 

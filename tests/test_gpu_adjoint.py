@@ -215,7 +215,7 @@ def test_gradient_matches_oracle_reverse_pass():
     st = {"E": w["E"], "B": w["B"], "species": w["species"]}
     st["rho"] = step.initial_rho(p, st["species"])
     L, adj = oadj.loss_and_gradient(p, st, 6, *w["probe"], checkpoint=4)
-    assert abs(float(loss) - L) < 1e-12 * L
+    assert abs(float(loss.detach()) - L) < 1e-12 * L
     for k, t in (("ux", ux), ("uy", uy), ("uz", uz)):
         r = adj["species"][0][k]
         assert np.linalg.norm(to_host(t.grad) - r) < 1e-10 * np.linalg.norm(r), k

@@ -198,6 +198,8 @@ def main():
     ap.add_argument("--e2e-copy-streams", type=int, default=1,
                     help="streams the per-step host-to-device input copies are spread over "
                          "(one measured fastest: 2.45e9 vs 2.28e9 particle-steps/s with four)")
+    ap.add_argument("--e2e-no-graph", action="store_true",
+                    help="end-to-end loop with direct pic_step calls instead of their CUDA graphs")
     ap.add_argument("--form", default="both", choices=["both", "fp32", "fp64"],
                     help="both: FP32 form timed as the headline, FP64 form beside it")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
@@ -388,6 +390,16 @@ def run_form(form, w, args, world, rank, local):
                     d.copy_(h, non_blocking=True)
                 copied[b][i].record(cs)
 
+    # the one-step call on each buffer set, captured as a CUDA graph (pic.StepGraph: the library
+    # takes every decision on the device, so the call replays exactly without its host launches)
+    graphs = []
+    if not args.e2e_no_graph:
+        capture = ctx.capture_step32 if fp32 else ctx.capture_step
+        for b in range(2):
+            for d, h in zip(bufs[b], host):
+                d.copy_(h)
+            Eb, Bb, rb, spb = sets[b]
+            graphs.append(capture(Eb, Bb, None, rb, spb, 1))
     for ev in done:
         ev.record(stream)
     torch.cuda.synchronize()
@@ -403,18 +415,23 @@ def run_form(form, w, args, world, rank, local):
         Eb, Bb, rb, spb = sets[b]
         for ev in copied[b]:
             stream.wait_event(ev)
-        step(Eb, Bb, None, rb, spb, 1)             # J^{n+1/2} is not part of the result: J = NULL
+        if graphs:
+            with torch.cuda.stream(stream):
+                graphs[b].replay()                  # pic_step(1) on set b, J = NULL
+        else:
+            step(Eb, Bb, None, rb, spb, 1)         # J^{n+1/2} is not part of the result: J = NULL
         done[b].record(stream)
         energy(Eb, Bb)                              # host reads the result back (synchronous)
     t1.record(stream)
     t1.synchronize()
     e2e_ms = t0.elapsed_time(t1)
-    del E2, B2, rho2, sp2, bufs, sets
+    del E2, B2, rho2, sp2, bufs, sets, graphs
     e2e_ms = max_over_ranks(e2e_ms, world)
     e2e = {"value": job_throughput(npart, ke, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": 8, "steps": ke,
            "note": "per step: pinned H2D of E, B, rho and all particles (double-buffered: the copy of "
-                   "step k+1 overlaps step k), pic_step(1), field energy read back"}
+                   "step k+1 overlaps step k), pic_step(1) (%s), field energy read back" %
+                   ("replayed as a CUDA graph, pic.StepGraph" if not args.e2e_no_graph else "direct call")}
 
     # ---- roofline of the dominant kernel (gather + push + deposit) ----
     push_ms, push_n = stage["push"]

@@ -163,7 +163,6 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    steps_total = args.warmup + args.steps
     # warm-up samples are run too (untimed) so that the timed steps see warm caches
     run_oracle_sample(args.workload, max(1, min(args.warmup, 1)))
     value, desc, secs, prm, n_sample = run_oracle_sample(args.workload, args.steps)
@@ -183,7 +182,6 @@ def reference_arm(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-    del steps_total
 
 
 def main():

@@ -191,11 +191,10 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_r2c_kernel(
   fft_tile<false>(sm, lay, M, tw, 2);
   // split: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W^k (Z_k - conj Z_{M-k}),  W = exp(-2 pi i / Nz)
   C* dst = out.p[comp];
-  const int nzh = M + 1, P = M / 2 + 1;
+  const int nzh = M + 1;
   const T h = (T)0.5;
   // k = 0 .. M/2 - 1 for every line (t < L M / 2), then k = M/2 (t >= L M / 2)
   const int lgH = lg2(M) - 1;
-  (void)P;
   for (int t = threadIdx.x; t < (L << lgH) + L; t += blockDim.x) {
     const bool mid = t >= (L << lgH);
     const int l = mid ? t - (L << lgH) : t >> lgH;

@@ -2,8 +2,8 @@
 
 Every entry point of the C ABI has a same-named method on :class:`Context`
 (``pic_step`` -> ``Context.step`` ...).  Field and particle arguments are
-torch CUDA tensors (float64, contiguous); the binding passes their device
-pointers and the context's stream.  All computation happens in the CUDA
+torch CUDA tensors (contiguous; float64 for the pic_step family, float32 and int32 cells for
+the pic_step32 family); the binding passes their device pointers and the context's stream.  All computation happens in the CUDA
 library: if it cannot be loaded this module raises at import time.
 """
 import ctypes

@@ -142,6 +142,9 @@ void pic_destroy(pic_ctx* ctx) {
     if (ctx->sp_off[q]) cudaFree(ctx->sp_off[q]);
     if (ctx->sp_chunk[q]) cudaFree(ctx->sp_chunk[q]);
   }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
   timers_free(ctx);
   delete ctx;
 }
@@ -238,6 +241,16 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
     return st;
   }
   ctx->rhoh[1] = ctx->rhoh[0] + nm;
+  if ((st = [&]() -> pic_status {
+         PIC_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+         PIC_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+         PIC_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+         return PIC_OK;
+       }()) != PIC_OK) {
+    fprintf(stderr, "pic_init: %s\n", ctx->err);
+    pic_destroy(ctx);
+    return st;
+  }
   if ((st = fft_setup(ctx)) != PIC_OK || (st = psatd_setup(ctx)) != PIC_OK) {
     fprintf(stderr, "pic_init: %s\n", ctx->err);
     pic_destroy(ctx);

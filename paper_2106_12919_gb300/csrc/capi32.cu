@@ -200,6 +200,50 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   const float* yee[6] = {E[0], E[1], E[2], B[0], B[1], B[2]};
   float* nodal6[6];
   for (int c = 0; c < 6; ++c) nodal6[c] = nodal(ctx) + c * nc;
+  const bool stag = ctx->cycle == PIC_CYCLE_STAGGERED;
+  const bool tiled = ctx->sort_interval > 0 && tiled_push_fits(ctx) && !stag;
+  int64_t total = 0;
+  for (int q = 0; q < n_species; ++q) total += sp[q].n;
+  if (tiled) {
+    // device scratch of the binning (allocated once; no allocation happens inside the steps)
+    if (!ctx->bin_gate) {
+      PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_gate, sizeof(int)));
+      PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_outside, sizeof(unsigned long long)));
+      PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->bin_outside, 0, sizeof(unsigned long long), ctx->stream));
+    }
+    for (int q = 0; q < n_species && q < PIC_MAX_BINNED_SPECIES; ++q) {
+      if (!ctx->sp_off[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
+      if (!ctx->sp_chunk[q] || ctx->sp_chunk_n[q] < sp[q].n) {
+        if (ctx->sp_chunk[q]) PIC_CUDA_TRY(ctx, cudaFree(ctx->sp_chunk[q]));
+        ctx->sp_chunk[q] = nullptr;
+        PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_chunk[q], tile_chunk_words(ctx, sp[q].n) * sizeof(uint32_t)));
+        ctx->sp_chunk_n[q] = sp[q].n;
+      }
+      ctx->sp_off_n[q] = sp[q].n;
+    }
+  }
+  // The first step's (forced) binning of species 0 reads the particles only: it runs on the
+  // context's second stream, concurrently with the entry transforms of the fields on this one,
+  // and the first push waits for it (fork / join by events, also valid inside graph capture).
+  const bool early_bin = tiled && n_species > 0;
+  if (early_bin) {
+    PIC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    PIC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    cudaStream_t main_stream = ctx->stream;
+    ctx->stream = ctx->aux;
+    pic_status st = PIC_OK;
+    {
+      StageScope t(ctx, STAGE_BIN, 1);
+      st = particles_bin32_decide(ctx, total, 1);
+    }
+    if (st == PIC_OK) {
+      StageScope t(ctx, STAGE_BIN, sp[0].n > 0 ? 12 : 9);
+      st = particles_bin32(ctx, &sp[0], ctx->sp_off[0], ctx->bin_gate, ctx->sp_chunk[0], false);
+    }
+    ctx->stream = main_stream;
+    if (st != PIC_OK) return st;
+    PIC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, ctx->aux));
+  }
   int cur = 0;
   if (!fd) {
     PIC_TRY32(load_fields32(ctx, cE, cB));
@@ -210,7 +254,6 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     StageScope t(ctx, STAGE_FFT, 3);
     PIC_TRY32(fft_r2c<float>(ctx, rin, rout, 1));
   }
-  const bool stag = ctx->cycle == PIC_CYCLE_STAGGERED;
   if (fd) {
     // E^n, B^n -> nodes in real space (work arrays: the nodal J buffer, free until the deposit)
     StageScope t(ctx, STAGE_OTHER, 9);
@@ -233,14 +276,6 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   const float* Bn[3] = {nd + 3 * nc, nd + 4 * nc, nd + 5 * nc};
   float* jn = Jn(ctx);
   float* Jnp[3] = {jn, jn + nc, jn + 2 * nc};
-  const bool tiled = ctx->sort_interval > 0 && tiled_push_fits(ctx) && !stag;
-  int64_t total = 0;
-  for (int q = 0; q < n_species; ++q) total += sp[q].n;
-  if (tiled && !ctx->bin_gate) {
-    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_gate, sizeof(int)));
-    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_outside, sizeof(unsigned long long)));
-    PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->bin_outside, 0, sizeof(unsigned long long), ctx->stream));
-  }
   int since_forced = 0;
   for (int s = 0; s < nsteps; ++s) {
     const bool last = s == nsteps - 1;
@@ -251,19 +286,9 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     if (tiled) {
       const int force = (s == 0 || since_forced >= ctx->sort_interval) ? 1 : 0;
       since_forced = force ? 1 : since_forced + 1;
-      {
+      if (!(s == 0 && early_bin)) {  // step 0: decided on the second stream
         StageScope t(ctx, STAGE_BIN, 1);
         PIC_TRY32(particles_bin32_decide(ctx, total, force));
-      }
-      for (int q = 0; q < n_species && q < PIC_MAX_BINNED_SPECIES; ++q) {
-        if (!ctx->sp_off[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
-        if (!ctx->sp_chunk[q] || ctx->sp_chunk_n[q] < sp[q].n) {
-          if (ctx->sp_chunk[q]) PIC_CUDA_TRY(ctx, cudaFree(ctx->sp_chunk[q]));
-          ctx->sp_chunk[q] = nullptr;
-          PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_chunk[q], tile_chunk_words(ctx, sp[q].n) * sizeof(uint32_t)));
-          ctx->sp_chunk_n[q] = sp[q].n;
-        }
-        ctx->sp_off_n[q] = sp[q].n;
       }
     }
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(jn, 0, 3 * nc * sizeof(float), ctx->stream));
@@ -272,7 +297,9 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
       if (tiled && q < PIC_MAX_BINNED_SPECIES) {
         // the binning leaves the sorted species in the shared scratch and the push copies it back
         // (so each species is binned right before its own push)
-        {
+        if (s == 0 && q == 0 && early_bin) {
+          PIC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));  // binned on the second stream
+        } else {
           StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 12 : 9);
           PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q], false));
         }

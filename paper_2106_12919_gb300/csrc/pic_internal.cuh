@@ -89,6 +89,8 @@ struct pic_ctx {
   int pusher;         // pic_pusher
   int cycle;          // pic_cycle
   cudaStream_t stream;
+  cudaStream_t aux;              // second stream (FP32 step: the first binning beside the entry transforms)
+  cudaEvent_t ev_fork, ev_join;  // fork / join events between stream and aux
   int64_t ncell, nzh, nmode;
   int ncoef;
   CenterWeights cw[3];

@@ -27,8 +27,12 @@
  *   as such.  Work buffers, coefficient tables and the spectral field state
  *   belong to the context.
  * Streams: all work is enqueued on the context's stream (pic_ext.cuda_stream,
- *   default: the legacy default stream).  Calls return once the work is
- *   enqueued, except those that return a host value (documented per call).
+ *   default: the legacy default stream).  pic_step32 runs the first binning of a
+ *   call on a second stream that the context owns, forked from and joined back
+ *   into the context's stream by events inside the call, so the caller sees the
+ *   ordering of the context's stream alone (and a call can be captured into a
+ *   CUDA graph on that stream).  Calls return once the work is enqueued, except
+ *   those that return a host value (documented per call).
  *   Kernel errors surface as PIC_ERR_CUDA at the next call or at pic_sync.
  * Errors: every call returns a pic_status and never aborts; pic_last_error
  *   gives a one-line description.  Arguments are validated before any launch.

@@ -247,10 +247,14 @@ class StepGraph:
     saves the host-side launch cost of each kernel (a step is 20-60 launches).  The call is
     made once uncaptured first (the context allocates its scratch for these particle counts
     then; capture forbids allocation), which advances the arrays by `nsteps`.  replay() runs
-    the call again on the current contents of the same arrays, on the current stream.
+    the call again on the current contents of the same arrays, on the current stream.  The
+    context must use a stream other than the legacy default stream.
     """
 
     def __init__(self, ctx, fn, args):
+        if ctx.stream.cuda_stream == 0:
+            raise ValueError("StepGraph needs a context created on a non-default stream (capture is not "
+                             "possible on the legacy default stream)")
         fn(*args)
         ctx.sync()
         self.graph = torch.cuda.CUDAGraph()

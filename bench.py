@@ -18,6 +18,7 @@ Under torchrun each rank runs an independent replica of the workload
 of the same workload per step (rank 0 only).
 """
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -83,11 +84,11 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, device):
         self.device = device
@@ -96,32 +97,36 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Median SM clock and the throttle reasons seen; with window = (t0, t1) (host wall
+        clock of the timed region) only the samples taken inside it, when there are any."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
-        sm, smax, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [r for r in rows if window and window[0] - 0.025 <= r[0] <= window[1] + 0.025]
+        use = inside or rows
+        reasons = {n for r in use for n, v in zip(names, r[3]) if v.lower().startswith("active")}
+        sm = [r[1] for r in use]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None, "reasons": sorted(reasons),
+                "samples": len(sm), "in_timed_region": bool(inside)}
 
 
 def max_over_ranks(x, world, device="cuda"):
@@ -337,15 +342,17 @@ def run_form(form, w, args, world, rank, local):
     torch.cuda.synchronize()
     ctx.timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
     e0.record(stream)
     step(E, B, J, rho, sp, args.steps)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
+    w1 = time.time()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    clocks = sampler.stop()
+    clocks = sampler.stop((w0, w1))
     stage = {s: ctx.timing_read(s) for s in ("push", "fft", "update", "bin", "other", "all")}
     ctx.timing(False)
     ms = max_over_ranks(ms, world)

@@ -97,3 +97,19 @@ def test_vacuum_dispersion_galilean_phases():
     ph = np.stack([v[2] * kc * dt + np.abs(ks) * dt, v[2] * kc * dt - np.abs(ks) * dt])
     ph = np.angle(np.exp(1j * ph))
     np.testing.assert_allclose(w, np.max(ph, axis=0) / dt, rtol=1e-11, atol=1e-12)
+
+
+def test_field_energy_uniform_fields_closed_form():
+    """W = 1/2 (eps0 |E|^2 + |B|^2 / mu0) V with mu0 = 1 / (eps0 c^2), for uniform fields and
+    c, eps0 different from 1."""
+    shape, dx, c, eps0 = (4, 6, 8), (0.5, 0.25, 2.0), 3.0, 0.7
+    E = [np.full(shape, 1.5), np.zeros(shape), np.full(shape, -2.0)]
+    B = [np.zeros(shape), np.full(shape, 0.5), np.zeros(shape)]
+    V = np.prod(shape) * np.prod(dx)
+    want = 0.5 * (eps0 * (1.5 ** 2 + 2.0 ** 2) + 0.5 ** 2 * eps0 * c * c) * V
+    assert abs(diagnostics.field_energy(E, B, dx, c=c, eps0=eps0) - want) < 1e-13 * want
+    # a box: the same density over its volume
+    lo, hi = (1, 2, 3), (3, 5, 8)
+    Vb = np.prod([hi[a] - lo[a] for a in range(3)]) * np.prod(dx)
+    wb = diagnostics.field_energy(E, B, dx, c=c, eps0=eps0, box_lo=lo, box_hi=hi)
+    assert abs(wb - want * Vb / V) < 1e-13 * want

@@ -164,3 +164,31 @@ def test_offset_grid_gather_is_exact_for_linear_fields_and_deposit_keeps_moments
     dV = np.prod(dx)
     assert abs(d.sum() * dV - w.sum()) < 1e-12 * w.sum()
     assert abs((d * Xg[0]).sum() * dV - (w * pos[0]).sum()) < 1e-11 * (w * pos[0]).sum()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_galilean_drift_and_midpoint_current(order):
+    """No fields: u is unchanged and the particle moves by dt (v - v_gal) (Galilean coordinates,
+    App. A.2); J^{n+1/2} is deposited at the midpoint x^n + dt (v - v_gal) / 2, so its first
+    moment sum_i x_i J_i dV is q w v times that midpoint (B-splines reproduce linear functions)."""
+    shape, dx, dt, c = (16, 16, 16), (0.5, 0.5, 0.5), 0.3, 1.0
+    v_gal = (0.1, -0.2, 0.6)
+    rng = np.random.default_rng(order)
+    n = 5
+    sp = {"x": rng.uniform(3.0, 5.0, n), "y": rng.uniform(3.0, 5.0, n), "z": rng.uniform(3.0, 5.0, n),
+          "ux": rng.normal(0, 0.5, n), "uy": rng.normal(0, 0.5, n), "uz": rng.normal(0, 0.5, n),
+          "w": rng.uniform(0.5, 1.5, n), "q": -1.0, "m": 1.0}
+    Z = [np.zeros(shape) for _ in range(3)]
+    out, J, rho = particles.push_and_deposit(sp, Z, Z, shape, dx, dt, order, v_gal, c)
+    g = np.sqrt(1 + sp["ux"] ** 2 + sp["uy"] ** 2 + sp["uz"] ** 2)
+    dV = np.prod(dx)
+    X = [np.arange(shape[a])[tuple(slice(None) if b == a else None for b in range(3))] * dx[a] for a in range(3)]
+    for a, (k, uk) in enumerate((("x", "ux"), ("y", "uy"), ("z", "uz"))):
+        assert np.array_equal(out[uk], sp[uk])
+        v = sp[uk] / g
+        assert np.allclose(out[k], sp[k] + dt * (v - v_gal[a]), rtol=0, atol=1e-13)
+        mid = sp[k] + 0.5 * dt * (v - v_gal[a])
+        # first moment of J_a along its own axis: sum_p q w v_a mid_a
+        assert abs(np.sum(X[a] * J[a]) * dV - np.sum(sp["q"] * sp["w"] * v * mid)) < 1e-12
+        # rho^{n+1} sits at x^{n+1}
+        assert abs(np.sum(X[a] * rho) * dV - np.sum(sp["q"] * sp["w"] * out[k])) < 1e-12

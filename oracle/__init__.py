@@ -29,7 +29,9 @@ diagnostics  Field energy (Sec. 2 (iii)), the L2 error norm (Sec. 5.2), the sten
              vacuum dispersion of an update (Sec. 2 (i), App. B).
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
-closed forms, brute force or invariants, except the full multi-step cycle,
-which is pinned only compositionally plus invariants (charge, cold-plasma
-oscillation, vacuum energy); beyond that the full step is "parity unpinned".
+closed forms, brute force or invariants.  The full multi-step cycle has no
+closed form; it is pinned by the pins of each of its stages, by invariants
+(charge, vacuum energy, the cold-plasma oscillation at omega_p) and by exact
+symmetries of the method that the whole cycle must keep (mirror reflection,
+exchange of two axes, translation by a cell: tests/test_oracle_symmetry.py).
 """

@@ -190,3 +190,16 @@ def test_fdtd_cycle_charge_and_vacuum():
         step.hybrid_step(p, st)
         assert abs(np.sum(st["rho"]) * np.prod(p.dx) - qtot) < 1e-12 * qabs
         assert all(np.all(np.isfinite(e)) for e in st["E"])
+
+
+@pytest.mark.parametrize("order", [2, 4, 8, 16, 32])
+def test_courant_bound_uses_the_largest_symbol(order):
+    """The Courant limit takes [k]_s at the Nyquist wave number: the symbol is monotone on
+    [0, pi/dx] (its derivative in k dx is the centering symbol zeta >= 0, App. C), so the
+    Nyquist value is the maximum over every wave number of the grid."""
+    N, dx = 64, 0.3
+    ks = np.abs(fornberg.k_staggered(N, dx, order).astype(np.float64))
+    ny = 2.0 * sum(w * (1 if n % 2 else -1) for n, w in enumerate(fdtd.fd_weights(order, dx), start=1))
+    assert abs(ks.max() - ny) < 1e-12 * ny
+    assert np.all(np.diff(ks[: N // 2 + 1]) > 0)        # signed indices 0..N/2-1, then the Nyquist -N/2
+    assert np.all(fornberg.zeta(N, order)[: N // 2 + 1].astype(np.float64) >= -1e-15)

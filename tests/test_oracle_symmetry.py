@@ -5,7 +5,8 @@ Under a reflection E and J are polar vectors and B an axial one; on the grid a c
 staggered along the reflected axis maps index i -> N-1-i, a nodal one i -> -i (mod N).  The
 exchange of two axes is an improper rotation as well (B picks up a sign).  These are symmetries of
 the continuous equations and of every discrete operator of the cycle (symmetric Fornberg
-centering, B-spline shapes, the k-space update on a symmetric k grid, the Boris push), so running
+centering, B-spline shapes, the k-space update on a symmetric k grid, the FDTD differences, the
+Boris push), so running
 the cycle on the transformed state must give the transformed result, to rounding.  A staggering
 offset, a phase sign, an axis mix-up or a one-sided stencil anywhere in the cycle breaks them."""
 import numpy as np
@@ -13,9 +14,6 @@ import pytest
 
 from oracle import grid, step
 from paper_2106_12919_gb300 import workloads
-
-POLAR = {"E": 1, "J": 1}
-
 
 def _reflect_x(a, name):
     """Mirror along x of the array of component `name` (E/B/J + x/y/z, or rho)."""
@@ -32,7 +30,7 @@ def _reflect_x(a, name):
     return sgn * f
 
 
-def _state(seed, shape=(8, 8, 16), ppc=2, variant=0, v=0.0, order=2):
+def _state(seed, shape=(8, 8, 16), ppc=2, variant=0, v=0.0, order=2, cycle=step.HYBRID):
     w = workloads.thermal_plasma(shape=shape, ppc=ppc, u_th=0.05)
     p = dict(w["params"])
     p.update(dx=(0.5, 0.5, 0.25), dt=0.2, shape_order=order, centering_order=(4, 4, 8), variant=variant,
@@ -41,7 +39,7 @@ def _state(seed, shape=(8, 8, 16), ppc=2, variant=0, v=0.0, order=2):
     E = [0.05 * rng.normal(size=shape) for _ in range(3)]
     B = [0.05 * rng.normal(size=shape) for _ in range(3)]
     sp = [dict(s) for s in w["species"]]
-    return step.Params(**p), E, B, sp
+    return step.Params(**p, cycle=cycle), E, B, sp
 
 
 def _run(prm, E, B, sp, nsteps=2):
@@ -56,9 +54,11 @@ def _close(a, b, scale):
     assert np.max(np.abs(a - b)) < 1e-12 * scale
 
 
-@pytest.mark.parametrize("variant,v,order", [(0, 0.0, 1), (0, 0.0, 2), (0, 0.0, 3), (1, 0.6, 2), (2, 0.5, 3)])
-def test_mirror_reflection_x(variant, v, order):
-    prm, E, B, sp = _state(1, variant=variant, v=v, order=order)
+@pytest.mark.parametrize("variant,v,order,cycle", [(0, 0.0, 1, 0), (0, 0.0, 2, 0), (0, 0.0, 3, 0), (1, 0.6, 2, 0),
+                                                   (2, 0.5, 3, 0), (0, 0.0, 2, step.STAGGERED),
+                                                   (0, 0.0, 3, step.HYBRID_FDTD)])
+def test_mirror_reflection_x(variant, v, order, cycle):
+    prm, E, B, sp = _state(1, variant=variant, v=v, order=order, cycle=cycle)
     L = prm.shape[0] * prm.dx[0]
     ref = _run(prm, E, B, sp)
     Er = [_reflect_x(E[a], grid.E_NAMES[a]) for a in range(3)]

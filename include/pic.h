@@ -117,7 +117,7 @@ typedef enum {
  *     in halves (B^{n+1/2} = B^n - (dt/2) curl E^n; E^{n+1} = E^n + dt (c^2 curl B^{n+1/2}
  *     - J^{n+1/2} / eps0); B^{n+1} = B^{n+1/2} - (dt/2) curl E^{n+1}), each derivative the
  *     staggered difference sum_n c_n (f_{j+n} - f_{j-n+1}) / dx with c_n = alpha^s_{m,n} /
- *     (2n - 1), 2m = spectral_order of the axis (0 means 2: Yee's scheme), whose symbol is
+ *     (2n - 1), 2m = spectral_order of the axis (0 means 2: Yee's scheme; at most 32), whose symbol is
  *     i [k]_s.  E, B are centered to the nodes and J to the Yee grid by the stencils of Sec. 3
  *     (Eq. staggered_finite_sum) in real space; filter_passes smooths the nodal J in real
  *     space before its centering.  rho is deposited (rho^{n+1} on exit) but the solver does

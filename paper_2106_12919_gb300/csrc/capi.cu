@@ -193,6 +193,10 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
   if (e.cycle < PIC_CYCLE_HYBRID || e.cycle > PIC_CYCLE_HYBRID_FDTD) return fail(PIC_ERR_ARG, "unknown cycle");
   if (e.cycle == PIC_CYCLE_HYBRID_FDTD && psatd_variant != PIC_PSATD_STANDARD)
     return fail(PIC_ERR_UNSUPPORTED, "the FDTD cycle has the standard (non-Galilean) update only");
+  if (e.cycle == PIC_CYCLE_HYBRID_FDTD)
+    for (int a = 0; a < 3; ++a)
+      if (e.spectral_order[a] / 2 > PIC_MAX_CENTER_M)
+        return fail(PIC_ERR_ARG, "FDTD difference order must be <= 32");
   if (e.reserved) return fail(PIC_ERR_ARG, "reserved fields must be 0");
   if (psatd_variant != PIC_PSATD_STANDARD) {
     if (!v_gal) return fail(PIC_ERR_ARG, "v_gal required");

@@ -99,6 +99,15 @@ def test_fdtd_cycle_validation_without_gpu_work():
 
     assert init(0.5, variant=1) == -2                    # Galilean
     assert init(0.5, variant=2) == -2                    # averaged Galilean
+    # difference order above 32 (the host weight table's size), refused before any device work
+    h = ctypes.c_void_p()
+    e = pic.PicExt()
+    pic.LIB.pic_ext_default(ctypes.byref(e))
+    e.cycle = pic.PIC_CYCLE_HYBRID_FDTD
+    e.spectral_order[:] = [2, 2, 64]
+    st = pic.LIB.pic_init(ctypes.byref(h), L3(16, 16, 128), D3(1, 1, 1), 0.01, 1, I3(8, 8, 8), 0, D3(0, 0, 0),
+                          ctypes.byref(e))
+    assert st == -1 and not h.value
     for dx, orders in (((1.0, 1.0, 1.0), (0, 0, 0)), ((0.2, 0.2, 0.04), (4, 4, 8)), ((1.0, 0.5, 2.0), (2, 6, 4))):
         lim = fdtd.courant_limit(tuple(o or 2 for o in orders), dx)
         assert init(lim * 1.001, dx=dx, orders=orders) == -1, (dx, orders)

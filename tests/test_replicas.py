@@ -74,3 +74,40 @@ def test_reference_arm_line_on_rank_zero():
                            "parallelism": "single"}
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_clock_sampler_keeps_the_samples_of_the_timed_region():
+    """bench.ClockSampler: nvidia-smi lines are parsed and only those stamped inside the timed
+    region enter the median and the throttle reasons (all of them when none falls inside)."""
+    import datetime
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def stamp(t):
+        return datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+
+    t0 = 1_800_000_000.0
+    lines = [
+        "0, 900, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active, %s" % stamp(t0 - 0.2),
+        "0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active, %s" % stamp(t0 + 0.01),
+        "0, 2055, 2070, 910.0, 0x0, Not Active, Not Active, Not Active, Not Active, %s" % stamp(t0 + 0.05),
+        "0, 600, 2070, 150.0, 0x0, Active, Not Active, Not Active, Not Active, %s" % stamp(t0 + 0.4),
+    ]
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def communicate(self, timeout=None):
+            return "\n".join(lines) + "\n", ""
+
+    s = bench.ClockSampler(0)
+    s.proc = FakeProc()
+    c = s.stop((t0, t0 + 0.06))
+    assert c["in_timed_region"] and c["samples"] == 2
+    assert c["sm_mhz"] == (2070 + 2055) / 2 and c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["sw_power_cap"]          # the hw_slowdown sample lies outside the region
+    s.proc = FakeProc()
+    c = s.stop((t0 + 10, t0 + 11))                  # no sample inside: all of them
+    assert not c["in_timed_region"] and c["samples"] == 4
+    assert "hw_slowdown" in c["reasons"]

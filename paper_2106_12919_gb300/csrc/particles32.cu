@@ -991,7 +991,8 @@ __device__ __forceinline__ void scatter32_one(const Scatter32Args& a, int64_t p)
   if (a.id_src) a.id_dst[q] = a.id_src[p];
 }
 
-// copy the sorted scratch back into the species arrays (8 words + optional id per particle)
+// copy the sorted scratch back into the species arrays (8 words + optional id per particle); used by
+// pic_bin32 only: inside pic_step32 the next tiled push reads the sorted copy instead
 struct CopyBackArgs {
   const int* gate;
   const uint32_t* src[8];

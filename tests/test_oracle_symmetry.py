@@ -15,19 +15,24 @@ import pytest
 from oracle import grid, step
 from paper_2106_12919_gb300 import workloads
 
-def _reflect_x(a, name):
-    """Mirror along x of the array of component `name` (E/B/J + x/y/z, or rho)."""
-    stag = grid.STAG[name][0]
-    f = np.flip(a, axis=0)
-    f = f if stag else np.roll(f, 1, axis=0)
+def _reflect(a, name, ax=0):
+    """Mirror along axis `ax` of the array of component `name` (E/B/J + x/y/z, or rho)."""
+    stag = grid.STAG[name][ax]
+    f = np.flip(a, axis=ax)
+    f = f if stag else np.roll(f, 1, axis=ax)
     kind, comp = (name[0], name[1:]) if name != "rho" else ("rho", "")
-    if kind in ("E", "J"):
-        sgn = -1.0 if comp == "x" else 1.0
-    elif kind == "B":
-        sgn = 1.0 if comp == "x" else -1.0
+    along = comp == "xyz"[ax]
+    if kind in ("E", "J"):        # polar: the component along the mirror axis flips
+        sgn = -1.0 if along else 1.0
+    elif kind == "B":             # axial: the two other components flip
+        sgn = 1.0 if along else -1.0
     else:
         sgn = 1.0
     return sgn * f
+
+
+def _reflect_x(a, name):
+    return _reflect(a, name, 0)
 
 
 def _state(seed, shape=(8, 8, 16), ppc=2, variant=0, v=0.0, order=2, cycle=step.HYBRID):
@@ -83,6 +88,29 @@ def test_mirror_reflection_x(variant, v, order, cycle):
         assert np.max(np.abs(dxp)) < 1e-12 * L
         _close(g["ux"], -r["ux"], 1.0)
         _close(g["uy"], r["uy"], 1.0)
+
+
+@pytest.mark.parametrize("ax", [1, 2])
+def test_mirror_reflection_y_and_z(ax):
+    prm, E, B, sp = _state(4 + ax, order=3)
+    L = prm.shape[ax] * prm.dx[ax]
+    ref = _run(prm, E, B, sp)
+    Er = [_reflect(E[a], grid.E_NAMES[a], ax) for a in range(3)]
+    Br = [_reflect(B[a], grid.B_NAMES[a], ax) for a in range(3)]
+    k, uk = "xyz"[ax], "u" + "xyz"[ax]
+    spr = []
+    for s in sp:
+        t = dict(s)
+        t[k] = np.mod(L - s[k], L)
+        t[uk] = -s[uk]
+        spr.append(t)
+    got = _run(prm, Er, Br, spr)
+    sE = max(np.abs(e).max() for e in ref["E"])
+    sB = max(np.abs(b).max() for b in ref["B"])
+    for a in range(3):
+        _close(got["E"][a], _reflect(ref["E"][a], grid.E_NAMES[a], ax), sE)
+        _close(got["B"][a], _reflect(ref["B"][a], grid.B_NAMES[a], ax), sB)
+    _close(got["rho"], _reflect(ref["rho"], "rho", ax), np.abs(ref["rho"]).max())
 
 
 def test_exchange_of_x_and_y():

@@ -49,3 +49,20 @@ def test_binding_refuses_to_load_without_the_library(tmp_path):
             "    print('loaded')\n") % (ROOT, str(tmp_path / "missing" / "libpic.so"))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("refused:"), r.stdout + r.stderr
+
+
+def test_bench_uses_the_oracle_only_for_its_cpu_legs():
+    """bench.py imports the oracle only inside run_oracle_sample (the cpu_baseline and the
+    reference arm), never at module level or on the timed path."""
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    top = set()
+    for node in tree.body:
+        if isinstance(node, ast.Import):
+            top.update(a.name.split(".")[0] for a in node.names)
+        elif isinstance(node, ast.ImportFrom) and node.module:
+            top.add(node.module.split(".")[0])
+    assert "oracle" not in top
+    users = [f.name for f in ast.walk(tree) if isinstance(f, ast.FunctionDef)
+             and any(isinstance(n, ast.ImportFrom) and n.module and n.module.split(".")[0] == "oracle"
+                     for n in ast.walk(f))]
+    assert users == ["run_oracle_sample"], users

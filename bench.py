@@ -321,8 +321,8 @@ def run_form(form, w, args, world, rank, local):
         J = [torch.zeros(ncell, dtype=tdt, device="cuda") for _ in range(3)]
         rho = torch.zeros(ncell, dtype=tdt, device="cuda")
         if fp32:
-            sp = [pic.Species32.from_positions(s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["q"],
-                                               s["m"], shape, p["dx"]) for s in w["species"]]
+            sp = [pic.Species32.from_positions(ctx, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"],
+                                               s["q"], s["m"]) for s in w["species"]]
         else:
             sp = [pic.Species(dev(s["x"]), dev(s["y"]), dev(s["z"]), dev(s["ux"]), dev(s["uy"]), dev(s["uz"]),
                               dev(s["w"]), s["q"], s["m"]) for s in w["species"]]

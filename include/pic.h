@@ -256,6 +256,22 @@ pic_status pic_adjoint_step(pic_ctx* ctx, const double* const E[3], const double
                             double* rhobar, const pic_species_adjoint* spbar);
 
 /*
+ * pic_field_energy_adjoint: the adjoint seed of the probe-box field energy, the loss of the
+ * reverse mode.  W = 1/2 sum (eps0 |E|^2 + |B|^2 / mu0) dV over the cells with index in
+ * [box_lo, box_hi) per axis of each Yee component (Sec. 2 (iii)), so
+ *   Ebar[c] = scale * eps0 dV E[c],  Bbar[c] = scale * dV B[c] / mu0  inside the box, 0 outside,
+ * with 1 / mu0 = eps0 c^2; scale is the gradient arriving from above (1 for dW itself).
+ *   E[3], B[3]        Yee fields (device, read only).
+ *   box_lo, box_hi    HOST int64[3] each, or both NULL for the whole grid (PIC_ERR_ARG for one
+ *                     NULL or a box outside [0, N)).
+ *   Ebar[3], Bbar[3]  device, overwritten over the whole grid; they must not overlap E or B.
+ * FP64 contexts only (PIC_ERR_ARG otherwise).  Asynchronous.
+ */
+pic_status pic_field_energy_adjoint(pic_ctx* ctx, const double* const E[3], const double* const B[3],
+                                    const int64_t box_lo[3], const int64_t box_hi[3], double scale,
+                                    double* const Ebar[3], double* const Bbar[3]);
+
+/*
  * pic_deposit_rho: rho (nodal, overwritten) = sum over species of the direct
  * charge deposition q w S(x - x_i) / dV at the current positions; use it to
  * form rho^0 before the first pic_step.  Asynchronous.
@@ -290,7 +306,9 @@ int64_t pic_num_tiles(const pic_ctx* ctx);
  * pic_center_to_nodal: finite-order centering of the six Yee components
  * F = {E^x, E^y, E^z, B^x, B^y, B^z} onto the nodal grid, as real-space stencils
  * (Sec. 3, Eq. staggered_finite_sum) applied along each staggered axis of each
- * component in x, y, z order, periodic wrap.  out[6] nodal, overwritten.
+ * component in x, y, z order, periodic wrap.  out[6] nodal, overwritten.  No out[c] may
+ * overlap any F[c'] or another out[c'] (a stencil pass would read neighbours it has already
+ * overwritten): such calls return PIC_ERR_ARG.
  * Asynchronous.
  */
 pic_status pic_center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);
@@ -299,7 +317,8 @@ pic_status pic_center_to_nodal(pic_ctx* ctx, const double* const F[6], double* c
  * pic_center_to_yee: finite-order centering of nodal J^x, J^y, J^z onto their
  * Yee positions, the mirror image of Eq. staggered_finite_sum:
  * f_{j+1/2} = sum_n alpha^s_{m,n} (f_{j+n} + f_{j-n+1}) / 2 along the staggered
- * axis of each component.  out[3] overwritten.  Asynchronous.
+ * axis of each component.  out[3] overwritten; no out[c] may overlap any Jn[c'] or another
+ * out[c'] (PIC_ERR_ARG).  Asynchronous.
  */
 pic_status pic_center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* const out[3]);
 
@@ -406,6 +425,25 @@ pic_status pic_field_energy32(pic_ctx* ctx, const float* const E[3], const float
 pic_status pic_total_charge32(pic_ctx* ctx, const float* rho, double* out);
 
 /*
+ * pic_species32_from_species: FP64 species -> FP32-form species, on the device.  Per
+ * coordinate, with t = x * (1/dx) rounded to FP64 (the multiply of the FP64 form's cell rule),
+ * cell index i = floor(t) and offset f = t - i (exact in FP64) rounded once to FP32; an offset
+ * that rounds to 1.0 becomes offset 0 of the next cell; the cell wraps into [0, N).  cell =
+ * (ix * Ny + iy) * Nz + iz.  ux, uy, uz, w are rounded to FP32; id is copied when both sides give
+ * one (PIC_ERR_ARG when only one does).  in->n must equal out->n; out's arrays are overwritten
+ * and must not overlap in's.  The paper holds positions in floating point only: the (cell,
+ * offset) form is the FP32 form's own representation.  Any context precision (only the grid and
+ * dx are used).  Asynchronous.
+ */
+pic_status pic_species32_from_species(pic_ctx* ctx, const pic_species* in, const pic_species32* out);
+
+/*
+ * pic_species32_to_species: the reverse: x = (i + f) dx in FP64 (i + f is exact), u and w
+ * widened to FP64, id copied as above.  Asynchronous.
+ */
+pic_status pic_species32_to_species(pic_ctx* ctx, const pic_species32* in, const pic_species* out);
+
+/*
  * ---- Diagnostics (not on the step's hot path; FP64 arithmetic; HOST results) ----
  *
  * pic_stencil_extent: stencil extent of the coefficient table `coef` (names as in
@@ -462,7 +500,8 @@ pic_status pic_beam_rms32(pic_ctx* ctx, const pic_species32* sp, double* delta);
  *   grid[3]             Nx, Ny, Nz: powers of two in [2, 1024], with
  *                       Nx * Ny * Nz <= 2,097,152 (2^21) cells, else PIC_ERR_CAPACITY.
  *   centering_order[3]  as in pic_init.
- *   F[6], out[6]        device arrays as in pic_center_to_nodal (caller-owned).
+ *   F[6], out[6]        device arrays as in pic_center_to_nodal (caller-owned); no out[c]
+ *                       may overlap any F[c'] or another out[c'] (PIC_ERR_ARG).
  *   cuda_stream         a cudaStream_t, or NULL for the legacy default stream.
  * Its scratch (the intermediate of the two-axis centering of B^x, B^y, B^z) is a
  * file-scope static device array of 2^21 doubles (16 MiB) that every GPU which

@@ -202,3 +202,32 @@ def tile_bins(pos, dx, grid_shape, tile):
     offsets = np.concatenate([[0], np.cumsum(counts)])
     order = np.argsort(tid, kind="stable")
     return tid, offsets, order
+
+
+def cell_offset_split(x, dx, N):
+    """Position of the FP32 form: integer cell index and FP32 offset inside that cell.
+
+    The paper keeps positions in floating point; the FP32 form holds each coordinate as an
+    integer cell i and an FP32 offset f in [0, 1) with x = (i + f) dx.  With t = x * (1/dx)
+    rounded to FP64 (the single multiply of shape_weights, so the cell agrees with the FP64
+    form's nearest-node rule), i = floor(t) and f = t - i (exact in FP64) rounded to FP32 once.
+    When that rounding gives 1.0 the particle is put at offset 0 of the next cell.  The cell
+    wraps periodically into [0, N).  Returns (i as int64, f as float32).
+    """
+    t = np.asarray(x, dtype=np.float64) * (1.0 / dx)
+    base = np.floor(t)
+    f = (t - base).astype(np.float32)
+    up = f == np.float32(1.0)
+    f = np.where(up, np.float32(0.0), f).astype(np.float32)
+    i = (base.astype(np.int64) + up.astype(np.int64)) % N
+    return i, f
+
+
+def cell_offset_join(i, f, dx):
+    """FP64 position x = (i + f) dx of a FP32-form coordinate (i + f is exact in FP64)."""
+    return (np.asarray(i, dtype=np.int64).astype(np.float64) + np.asarray(f, dtype=np.float32).astype(np.float64)) * dx
+
+
+def linear_cell(ix, iy, iz, shape):
+    """Linear cell index (ix * Ny + iy) * Nz + iz of the C-order [Nx][Ny][Nz] grid."""
+    return (np.asarray(ix, dtype=np.int64) * shape[1] + iy) * shape[2] + iz

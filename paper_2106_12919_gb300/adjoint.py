@@ -20,7 +20,7 @@ from . import pic
 class Rollout:
     """Static part of a differentiable run: context, positions and weights, steps, probe box."""
 
-    def __init__(self, ctx, species, nsteps, box_lo, box_hi, checkpoint=10, dx=None, eps0=1.0, c=1.0):
+    def __init__(self, ctx, species, nsteps, box_lo, box_hi, checkpoint=10):
         if ctx.precision != pic.PIC_FP64:
             raise ValueError("the differentiable form is FP64")
         if ctx.sort_interval != 0:
@@ -29,7 +29,6 @@ class Rollout:
             raise ValueError("ProbeEnergy differentiates one species")
         self.ctx, self.species, self.nsteps = ctx, species, int(nsteps)
         self.lo, self.hi, self.K = tuple(box_lo), tuple(box_hi), int(checkpoint)
-        self.dx, self.eps0, self.c = dx, eps0, c
 
 
 def _clone_state(E, B, rho, sp):
@@ -69,14 +68,11 @@ class ProbeEnergy(torch.autograd.Function):
         run = fctx.run
         ctx = run.ctx
         Ec, Bc = fctx.final
-        shape = ctx.shape
-        mask = torch.zeros(shape, dtype=torch.float64, device=Ec[0].device)
-        mask[run.lo[0]:run.hi[0], run.lo[1]:run.hi[1], run.lo[2]:run.hi[2]] = 1.0
-        mask = mask.reshape(Ec[0].shape)
-        dV = run.dx[0] * run.dx[1] * run.dx[2]
-        inv_mu0 = run.eps0 * run.c * run.c
-        Eb = [run.eps0 * dV * Ec[a] * mask for a in range(3)]      # d W / d E of the probe box
-        Bb = [inv_mu0 * dV * Bc[a] * mask for a in range(3)]
+        # the seed g dW/dE, g dW/dB of the probe box (pic_field_energy_adjoint); every adjoint
+        # below is linear in it, so the returned gradients already carry the factor g
+        Eb = [torch.empty_like(Ec[0]) for _ in range(3)]
+        Bb = [torch.empty_like(Ec[0]) for _ in range(3)]
+        ctx.field_energy_adjoint(Ec, Bc, run.lo, run.hi, float(gout), Eb, Bb)
         rhob = torch.zeros_like(Ec[0])
         spb = [{k: torch.zeros_like(s.x) for k in ("x", "y", "z", "ux", "uy", "uz")} for s in run.species]
         for s0 in sorted(fctx.ckpt, reverse=True):
@@ -91,7 +87,4 @@ class ProbeEnergy(torch.autograd.Function):
             for n in range(s1 - 1, s0 - 1, -1):
                 Es, Bs, _, sps = states[n - s0]
                 ctx.adjoint_step(Es, Bs, sps, Eb, Bb, rhob, spb)
-        g = gout.to(torch.float64)
-        gE = torch.stack(Eb) * g
-        gB = torch.stack(Bb) * g
-        return gE, gB, spb[0]["ux"] * g, spb[0]["uy"] * g, spb[0]["uz"] * g, None
+        return torch.stack(Eb), torch.stack(Bb), spb[0]["ux"], spb[0]["uy"], spb[0]["uz"], None

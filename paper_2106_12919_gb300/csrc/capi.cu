@@ -308,6 +308,9 @@ pic_status pic_center_to_nodal(pic_ctx* ctx, const double* const F[6], double* c
   if (!ctx) return PIC_ERR_ARG;
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(F, 6) || !all_nonnull(out, 6)) return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
+  if (arrays_overlap(reinterpret_cast<const void* const*>(F), 6, reinterpret_cast<const void* const*>(out), 6,
+                     ctx->ncell * sizeof(double)))
+    return pic_set_error(ctx, PIC_ERR_ARG, "an output array overlaps an input or another output");
   return center_to_nodal(ctx, F, out);
 }
 
@@ -315,6 +318,9 @@ pic_status pic_center_to_yee(pic_ctx* ctx, const double* const Jn[3], double* co
   if (!ctx) return PIC_ERR_ARG;
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(Jn, 3) || !all_nonnull(out, 3)) return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
+  if (arrays_overlap(reinterpret_cast<const void* const*>(Jn), 3, reinterpret_cast<const void* const*>(out), 3,
+                     ctx->ncell * sizeof(double)))
+    return pic_set_error(ctx, PIC_ERR_ARG, "an output array overlaps an input or another output");
   return center_to_yee(ctx, Jn, out);
 }
 

@@ -104,6 +104,9 @@ extern "C" pic_status pic_center_to_nodal_static(const int64_t grid[3], const in
             (long long)ncell, (long long)kStaticScratchCells);
     return PIC_ERR_CAPACITY;
   }
+  if (arrays_overlap(reinterpret_cast<const void* const*>(F), 6, reinterpret_cast<const void* const*>(out), 6,
+                     (size_t)ncell * sizeof(double)))
+    return PIC_ERR_ARG;  // stencil passes cannot run in place
   double* scratch = nullptr;
   const pic_status st = scratch_address(&scratch);
   if (st != PIC_OK) return st;

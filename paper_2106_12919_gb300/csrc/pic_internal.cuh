@@ -177,6 +177,23 @@ pic_status pic_set_error(pic_ctx* ctx, pic_status st, const char* fmt, ...);
     if (s_ != PIC_OK) return s_; \
   } while (0)
 
+// True when an output array overlaps an input array or another output array, each `bytes` long
+// (stencil passes read neighbours, so they cannot run in place).
+inline bool arrays_overlap(const void* const* in, int nin, const void* const* out, int nout, size_t bytes) {
+  auto hit = [bytes](const void* a, const void* b) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    return pa < pb + bytes && pb < pa + bytes;
+  };
+  for (int o = 0; o < nout; ++o) {
+    for (int i = 0; i < nin; ++i)
+      if (hit(out[o], in[i])) return true;
+    for (int q = o + 1; q < nout; ++q)
+      if (hit(out[o], out[q])) return true;
+  }
+  return false;
+}
+
 // Component pointer bundles passed by value to kernels.
 template <class T> struct RP6 { T* p[6]; };
 template <class T> struct CRP6 { const T* p[6]; };

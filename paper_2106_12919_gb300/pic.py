@@ -103,6 +103,10 @@ def _load():
         "pic_vacuum_dispersion": (ctypes.c_int, [_vp, ctypes.c_int, P(ctypes.c_double)]),
         "pic_beam_rms": (ctypes.c_int, [_vp, P(PicSpecies), P(ctypes.c_double)]),
         "pic_beam_rms32": (ctypes.c_int, [_vp, P(PicSpecies32), P(ctypes.c_double)]),
+        "pic_species32_from_species": (ctypes.c_int, [_vp, P(PicSpecies), P(PicSpecies32)]),
+        "pic_species32_to_species": (ctypes.c_int, [_vp, P(PicSpecies32), P(PicSpecies)]),
+        "pic_field_energy_adjoint": (ctypes.c_int, [_vp, P(_vp), P(_vp), P(ctypes.c_int64), P(ctypes.c_int64),
+                                                    ctypes.c_double, P(_vp), P(_vp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -119,7 +123,7 @@ EXPORTS = ("pic_ext_default", "pic_init", "pic_destroy", "pic_last_error", "pic_
            "pic_center_to_nodal_static", "pic_step32", "pic_deposit_rho32", "pic_push_deposit32", "pic_bin32",
            "pic_fft_forward32", "pic_fft_inverse32", "pic_field_energy32", "pic_total_charge32",
            "pic_adjoint_step", "pic_stencil_extent", "pic_axis_tables", "pic_vacuum_dispersion", "pic_beam_rms",
-           "pic_beam_rms32")
+           "pic_beam_rms32", "pic_species32_from_species", "pic_species32_to_species", "pic_field_energy_adjoint")
 
 
 def _ptr(t, n=None):
@@ -196,35 +200,25 @@ class Species32:
         return PicSpecies32(n, self.q, self.m, *p, _ptr(self.id, n) if self.id is not None else None)
 
     @staticmethod
-    def from_positions(x, y, z, ux, uy, uz, w, q, m, shape, dx, device="cuda", id=None):
-        """Host float64 positions -> (cell, offsets) layout on the device (marshalling only)."""
-        import numpy as np
-        idx, off = [], []
-        for a, xa in enumerate((x, y, z)):
-            t = np.asarray(xa, dtype=np.float64) / dx[a]
-            i = np.floor(t)
-            f = (t - i).astype(np.float32)
-            up = f >= np.float32(1.0)            # offset rounded up to 1 in float32
-            f = np.where(up, np.float32(0.0), f)
-            i = (i.astype(np.int64) + up) % shape[a]
-            idx.append(i)
-            off.append(f)
-        cell = ((idx[0] * shape[1] + idx[1]) * shape[2] + idx[2]).astype(np.int32)
-        dev = lambda v, dt: torch.from_numpy(np.ascontiguousarray(v, dtype=dt)).to(device)
-        return Species32(dev(cell, np.int32), dev(off[0], np.float32), dev(off[1], np.float32),
-                         dev(off[2], np.float32), dev(ux, np.float32), dev(uy, np.float32), dev(uz, np.float32),
-                         dev(w, np.float32), q, m, id=id)
+    def from_positions(ctx, x, y, z, ux, uy, uz, w, q, m, id=None):
+        """FP64 positions, momenta and weights (host arrays or CUDA tensors) -> a new FP32-form
+        species on the device, split by pic_species32_from_species on ctx's stream."""
+        return ctx.species32_from_species(Species(*[_as_dev64(a) for a in (x, y, z, ux, uy, uz, w)], q, m, id=id))
 
-    def positions(self, shape, dx):
-        """Device (cell, offsets) -> host float64 positions x, y, z."""
-        import numpy as np
-        c = self.cell.cpu().numpy().astype(np.int64)
-        iz = c % shape[2]
-        iy = (c // shape[2]) % shape[1]
-        ix = c // (shape[1] * shape[2])
-        return [(ix + self.fx.cpu().numpy().astype(np.float64)) * dx[0],
-                (iy + self.fy.cpu().numpy().astype(np.float64)) * dx[1],
-                (iz + self.fz.cpu().numpy().astype(np.float64)) * dx[2]]
+    def positions(self, ctx):
+        """Host FP64 positions [x, y, z] = (cell + offset) dx, formed on the device by
+        pic_species32_to_species."""
+        s64 = ctx.species32_to_species(self)
+        ctx.sync()
+        return [s64.x.cpu().numpy(), s64.y.cpu().numpy(), s64.z.cpu().numpy()]
+
+
+def _as_dev64(a):
+    """A host array or tensor as a contiguous CUDA float64 tensor (a copy, no arithmetic)."""
+    if isinstance(a, torch.Tensor):
+        return a.to(device="cuda", dtype=torch.float64).contiguous()
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
 def _species_array(species):
@@ -428,6 +422,40 @@ class Context:
         out = ctypes.c_double()
         self._check(LIB.pic_total_charge32(self.h, _ptr(rho, self.ncell), ctypes.byref(out)))
         return out.value
+
+    def _ordered(self, fn, *args):
+        """Call fn(ctx, *args) on the context's stream, ordered after the work already queued on
+        torch's current stream (which made the inputs) and before the work queued there next."""
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        self._check(fn(self.h, *args))
+        cur.wait_stream(self.stream)
+
+    def species32_from_species(self, sp):
+        """pic_species32_from_species: a new FP32-form species (device) from an FP64 one."""
+        n = sp.n
+        f = lambda: torch.empty(n, dtype=torch.float32, device="cuda")
+        out = Species32(torch.empty(n, dtype=torch.int32, device="cuda"), f(), f(), f(), f(), f(), f(), f(),
+                        sp.q, sp.m, id=torch.empty(n, dtype=torch.int64, device="cuda") if sp.id is not None else None)
+        self._ordered(LIB.pic_species32_from_species, ctypes.byref(sp.c_struct()), ctypes.byref(out.c_struct()))
+        return out
+
+    def species32_to_species(self, sp32):
+        """pic_species32_to_species: a new FP64 species (device) from an FP32-form one."""
+        n = sp32.n
+        f = lambda: torch.empty(n, dtype=torch.float64, device="cuda")
+        out = Species(f(), f(), f(), f(), f(), f(), f(), sp32.q, sp32.m,
+                      id=torch.empty(n, dtype=torch.int64, device="cuda") if sp32.id is not None else None)
+        self._ordered(LIB.pic_species32_to_species, ctypes.byref(sp32.c_struct()), ctypes.byref(out.c_struct()))
+        return out
+
+    def field_energy_adjoint(self, E, B, box_lo, box_hi, scale, Ebar, Bbar):
+        """pic_field_energy_adjoint: Ebar, Bbar (overwritten) = scale * dW/dE, dW/dB of the box."""
+        n = self.ncell
+        lo = _l3(*box_lo) if box_lo is not None else None
+        hi = _l3(*box_hi) if box_hi is not None else None
+        self._check(LIB.pic_field_energy_adjoint(self.h, _parr(E, n), _parr(B, n), lo, hi, float(scale),
+                                                 _parr(Ebar, n), _parr(Bbar, n)))
 
     # ---- diagnostics (host results) ----
     def _axis_len(self, axis):

@@ -43,6 +43,10 @@ int main(void) {
   if (strcmp(pic_last_error(NULL), "null context") != 0) return fail("pic_last_error(NULL)");
   if (pic_step(NULL, NULL, NULL, NULL, NULL, NULL, 0, 1) != PIC_ERR_ARG) return fail("pic_step(NULL)");
   if (pic_num_tiles(NULL) != -1) return fail("pic_num_tiles(NULL)");
+  if (pic_species32_from_species(NULL, NULL, NULL) != PIC_ERR_ARG) return fail("pic_species32_from_species(NULL)");
+  if (pic_species32_to_species(NULL, NULL, NULL) != PIC_ERR_ARG) return fail("pic_species32_to_species(NULL)");
+  if (pic_field_energy_adjoint(NULL, NULL, NULL, NULL, NULL, 1.0, NULL, NULL) != PIC_ERR_ARG)
+    return fail("pic_field_energy_adjoint(NULL)");
   pic_destroy(NULL);
   printf("ok\n");
   return 0;

@@ -111,3 +111,25 @@ def test_fdtd_cycle_validation_without_gpu_work():
     for dx, orders in (((1.0, 1.0, 1.0), (0, 0, 0)), ((0.2, 0.2, 0.04), (4, 4, 8)), ((1.0, 0.5, 2.0), (2, 6, 4))):
         lim = fdtd.courant_limit(tuple(o or 2 for o in orders), dx)
         assert init(lim * 1.001, dx=dx, orders=orders) == -1, (dx, orders)
+
+
+def test_centering_rejects_overlapping_arrays_without_gpu_work():
+    """pic_center_to_nodal_static refuses outputs that overlap an input or another output before
+    any device call (the stencil passes cannot run in place).  The addresses are never used."""
+    import ctypes
+    from paper_2106_12919_gb300 import pic
+    L3, I3, P6 = ctypes.c_int64 * 3, ctypes.c_int32 * 3, ctypes.c_void_p * 6
+    ncell = 8 * 8 * 16
+    nbytes = ncell * 8
+    base = 1 << 40
+    F = P6(*[base + c * nbytes for c in range(6)])
+    outs = [base + (6 + c) * nbytes for c in range(6)]
+    cases = {"in place": 0, "into a later input": 3 * nbytes, "half overlap": nbytes // 2}
+    for what, off in cases.items():
+        o = list(outs)
+        o[2] = base + off
+        st = pic.LIB.pic_center_to_nodal_static(L3(8, 8, 16), I3(4, 4, 4), F, P6(*o), None)
+        assert st == -1, what
+    o = list(outs)
+    o[4] = o[1]
+    assert pic.LIB.pic_center_to_nodal_static(L3(8, 8, 16), I3(4, 4, 4), F, P6(*o), None) == -1

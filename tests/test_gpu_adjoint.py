@@ -62,7 +62,7 @@ def _probe_run(shape, ppc, steps, K, amplitude=0.01, order=1):
     ctx = context_for(p, sort_interval=0)
     (sp,) = species_to_dev(w["species"], with_id=False)
     lo, hi = w["probe"]
-    run = gadj.Rollout(ctx, [sp], steps, lo, hi, checkpoint=K, dx=p["dx"], eps0=p["eps0"], c=p["c"])
+    run = gadj.Rollout(ctx, [sp], steps, lo, hi, checkpoint=K)
     profile = to_dev(w["E"][0] / amplitude)
     E0 = torch.stack([to_dev(a) for a in w["E"]])
     B0 = torch.stack([to_dev(a) for a in w["B"]])

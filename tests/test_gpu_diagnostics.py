@@ -83,9 +83,9 @@ def test_beam_rms_fp64_and_fp32():
     (sp,) = species_to_dev([beam], with_id=False)
     assert abs(ctx.beam_rms(sp) - ref) < 1e-12 * ref
     ctx32 = context_for(p, precision=pic.PIC_FP32)
-    s32 = pic.Species32.from_positions(beam["x"], beam["y"], beam["z"], beam["ux"], beam["uy"], beam["uz"],
-                                       beam["w"], beam["q"], beam["m"], p["shape"], p["dx"])
-    x, y, _ = s32.positions(p["shape"], p["dx"])
+    s32 = pic.Species32.from_positions(ctx32, beam["x"], beam["y"], beam["z"], beam["ux"], beam["uy"], beam["uz"],
+                                       beam["w"], beam["q"], beam["m"])
+    x, y, _ = s32.positions(ctx32)
     w32 = s32.w.cpu().numpy().astype(np.float64)
     ref32 = diagnostics.beam_rms(x, y, w32)
     assert abs(ctx32.beam_rms32(s32) - ref32) < 1e-12 * ref32

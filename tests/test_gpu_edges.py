@@ -97,8 +97,8 @@ def test_step_with_an_empty_species(fp32):
         if fp32:
             ctx = context_for(p, sort_interval=2, precision=pic.PIC_FP32)
             dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
-            sp = [pic.Species32.from_positions(s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["q"],
-                                               s["m"], shape, dx) for s in sps]
+            sp = [pic.Species32.from_positions(ctx, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"],
+                                               s["q"], s["m"]) for s in sps]
             E, B = [dev(a) for a in w["E"]], [dev(a) for a in w["B"]]
             rho = torch.empty(ctx.ncell, dtype=torch.float32, device="cuda")
             ctx.deposit_rho32(sp, rho)
@@ -138,12 +138,11 @@ def test_tiled_push_chunk_boundaries():
     E0 = [rng.normal(size=shape) * 0.1 for _ in range(3)]
     B0 = [np.zeros(shape) for _ in range(3)]
     ctx = context_for(p, sort_interval=1, precision=pic.PIC_FP32)
-    (d,) = [pic.Species32.from_positions(sp["x"], sp["y"], sp["z"], sp["ux"], sp["uy"], sp["uz"], sp["w"],
-                                         sp["q"], sp["m"], shape, dx,
-                                         id=torch.arange(x.size, dtype=torch.int64, device="cuda"))]
+    (d,) = [pic.Species32.from_positions(ctx, sp["x"], sp["y"], sp["z"], sp["ux"], sp["uy"], sp["uz"], sp["w"],
+                                         sp["q"], sp["m"], id=torch.arange(x.size, dtype=torch.int64, device="cuda"))]
     # the oracle gets the same (cell, FP32 offset) particles in FP64
     order = np.argsort(to_host(d.id))
-    px, py, pz = d.positions(shape, dx)
+    px, py, pz = d.positions(ctx)
     ref_sp = {"x": px[order], "y": py[order], "z": pz[order], "q": sp["q"], "m": sp["m"]}
     for k in ("ux", "uy", "uz", "w"):
         ref_sp[k] = to_host(getattr(d, k)).astype(np.float64)[order]

@@ -22,24 +22,24 @@ def dev32(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def species32(sp_list, shape, dx):
+def species32(ctx, sp_list):
+    """FP64 host particles -> FP32-form species on the device (split by pic_species32_from_species)."""
     import torch
     from paper_2106_12919_gb300 import pic
     out = []
     for s in sp_list:
         n = s["x"].size
-        out.append(pic.Species32.from_positions(s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"],
-                                                s["q"], s["m"], shape, dx,
-                                                id=torch.arange(n, dtype=torch.int64, device="cuda")))
+        out.append(pic.Species32.from_positions(ctx, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"],
+                                                s["q"], s["m"], id=torch.arange(n, dtype=torch.int64, device="cuda")))
     return out
 
 
-def as_oracle_species(sp32, shape, dx):
+def as_oracle_species(ctx, sp32):
     """The FP32-form particle set in the oracle's FP64 layout (same particles, original order)."""
     out = []
     for s in sp32:
         order = np.argsort(to_host(s.id))
-        x, y, z = s.positions(shape, dx)
+        x, y, z = s.positions(ctx)
         d = {"x": x[order], "y": y[order], "z": z[order]}
         for k in ("ux", "uy", "uz", "w"):
             d[k] = to_host(getattr(s, k)).astype(np.float64)[order]
@@ -91,8 +91,8 @@ def test_push_deposit32(order, variant, v):
            "w": rng.uniform(0.5, 1.5, n), "q": -1.0, "m": 1.0}]
     En = [rng.normal(size=shape).astype(np.float32).astype(np.float64) for _ in range(3)]
     Bn = [rng.normal(size=shape).astype(np.float32).astype(np.float64) for _ in range(3)]
-    d32 = species32(sp, shape, dx)
-    ref_sp = as_oracle_species(d32, shape, dx)
+    d32 = species32(ctx, sp)
+    ref_sp = as_oracle_species(ctx, d32)
     new_ref, Jref, rref = particles.push_and_deposit(ref_sp[0], En, Bn, shape, dx, dt, order, v)
     Jd = [torch.empty(ctx.ncell, dtype=torch.float32, device="cuda") for _ in range(3)]
     rd = torch.empty(ctx.ncell, dtype=torch.float32, device="cuda")
@@ -100,7 +100,7 @@ def test_push_deposit32(order, variant, v):
     ctx.sync()
     assert field_rel_err([to_host(a).reshape(shape) for a in Jd], Jref) < 2e-6
     assert field_rel_err([to_host(rd).reshape(shape)], [rref]) < 2e-6
-    (g,) = as_oracle_species(d32, shape, dx)
+    (g,) = as_oracle_species(ctx, d32)
     for a, k in enumerate(("x", "y", "z")):
         assert np.max(periodic_pos_err(g[k], new_ref[k], L[a])) < 1e-6 * L[a]
     for k in ("ux", "uy", "uz"):
@@ -117,7 +117,7 @@ def test_bin32_offsets_exact():
     n = 50000
     sp = [{"x": rng.uniform(0, 16, n), "y": rng.uniform(0, 16, n), "z": rng.uniform(0, 16, n),
            "ux": np.zeros(n), "uy": np.zeros(n), "uz": np.zeros(n), "w": np.ones(n), "q": -1.0, "m": 1.0}]
-    (d,) = species32(sp, shape, dx)
+    (d,) = species32(ctx, sp)
     cell = to_host(d.cell).astype(np.int64)
     iz, iy, ix = cell % shape[2], (cell // shape[2]) % shape[1], cell // (shape[1] * shape[2])
     nt = [shape[a] // tile[a] for a in range(3)]
@@ -150,7 +150,7 @@ def test_bin32_sorted_input_is_left_in_place():
     sp = [{"x": rng.uniform(0, 16, n), "y": rng.uniform(0, 16, n), "z": rng.uniform(0, 16, n),
            "ux": rng.normal(size=n), "uy": rng.normal(size=n), "uz": rng.normal(size=n), "w": rng.uniform(size=n),
            "q": -1.0, "m": 1.0}]
-    (d,) = species32(sp, shape, dx)
+    (d,) = species32(ctx, sp)
     off1 = torch.empty(ctx.num_tiles() + 1, dtype=torch.int64, device="cuda")
     off2 = torch.empty_like(off1)
     ctx.bin32(d, off1)
@@ -177,7 +177,7 @@ def test_step32_without_J(cycle):
     outs = []
     for with_j in (True, False):
         ctx = ctx32(p, sort_interval=10, **opts)
-        sp = species32(w["species"], p["shape"], p["dx"])
+        sp = species32(ctx, w["species"])
         E = [dev32(a) for a in w["E"]]
         B = [dev32(a) for a in w["B"]]
         J = [torch.empty(ctx.ncell, dtype=torch.float32, device="cuda") for _ in range(3)] if with_j else None
@@ -185,7 +185,7 @@ def test_step32_without_J(cycle):
         ctx.deposit_rho32(sp, rho)
         ctx.step32(E, B, J, rho, sp, 5)
         ctx.sync()
-        (o,) = as_oracle_species(sp, p["shape"], p["dx"])
+        (o,) = as_oracle_species(ctx, sp)
         outs.append(([to_host(t).astype(np.float64) for t in E + B + [rho]], o))
     (f1, s1), (f2, s2) = outs
     assert field_rel_err(f2[:6], f1[:6]) < 1e-6
@@ -275,11 +275,11 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
         w["species"] = [{k: (v[s["z"] < half] if isinstance(v, np.ndarray) else v) for k, v in s.items()}
                         for s in w["species"]]
     ctx = ctx32(p, sort_interval=10, **opts)
-    sp = species32(w["species"], shape, dx)
+    sp = species32(ctx, w["species"])
     op = step.Params(**p, **opts)
     E0 = [a.astype(np.float32).astype(np.float64) for a in w["E"]]
     B0 = [a.astype(np.float32).astype(np.float64) for a in w["B"]]
-    sp0 = as_oracle_species(sp, shape, dx)
+    sp0 = as_oracle_species(ctx, sp)
     st = _oracle_run(op, E0, B0, sp0, nsteps)
     bound = 1e-5
     if chaotic:
@@ -300,7 +300,7 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
     per_comp = {k + "xyz"[a]: float(np.linalg.norm(g([t])[0] - st[k][a]) / max(np.linalg.norm(st[k][a]), 1e-300))
                 for k, ts in (("E", E), ("B", B)) for a, t in enumerate(ts)}
     mom = {}
-    for s_ref, s_gpu in zip(st["species"], as_oracle_species(sp, shape, dx)):
+    for s_ref, s_gpu in zip(st["species"], as_oracle_species(ctx, sp)):
         for k in ("ux", "uy", "uz"):
             mom[k] = float(np.linalg.norm(s_gpu[k] - s_ref[k]) / max(np.linalg.norm(s_ref[k]), 1e-300))
     print("\n%s after %d steps: fields %s\n per component %s\n momenta %s" % (name, nsteps, errs, per_comp, mom))

@@ -105,10 +105,10 @@ def test_fullsize_sampled_particles_and_charge_fp32(wf):
     ctx = context_for(p, precision=pic.PIC_FP32)
     s = wf["species"][0]
     n = s["x"].size
-    sp = pic.Species32.from_positions(s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["q"], s["m"],
-                                      FULL, p["dx"], id=torch.arange(n, dtype=torch.int64, device="cuda"))
+    sp = pic.Species32.from_positions(ctx, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["q"], s["m"],
+                                      id=torch.arange(n, dtype=torch.int64, device="cuda"))
     # the oracle starts from the same particle set: positions as the FP32 form holds them
-    x0 = sp.positions(FULL, p["dx"])
+    x0 = sp.positions(ctx)
     wf32 = dict(wf)
     wf32["species"] = [dict(s, x=x0[0], y=x0[1], z=x0[2])]
     wf32["E"] = [a.astype(np.float32).astype(np.float64) for a in wf["E"]]
@@ -125,7 +125,7 @@ def test_fullsize_sampled_particles_and_charge_fp32(wf):
     ids = to_host(sp.id)
     where = np.empty(n, dtype=np.int64)
     where[ids] = np.arange(n)
-    pos = sp.positions(FULL, p["dx"])
+    pos = sp.positions(ctx)
     L = [FULL[a] * p["dx"][a] for a in range(3)]
     for a in range(3):
         assert np.max(periodic_pos_err(pos[a][where[idx]], new_ref[a], L[a])) < 2e-6 * L[a] / FULL[a] * 8

@@ -24,8 +24,8 @@ def test_graph_replay_matches_direct_call(fp32):
 
     def fresh():
         if fp32:
-            sp = [pic.Species32.from_positions(s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"], s["q"],
-                                               s["m"], shape, dx) for s in w["species"]]
+            sp = [pic.Species32.from_positions(ctx, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], s["w"],
+                                               s["q"], s["m"]) for s in w["species"]]
         else:
             sp = species_to_dev(w["species"], with_id=False)
         return [dev(a) for a in w["E"]], [dev(a) for a in w["B"]], torch.zeros(ctx.ncell, dtype=dev(w["E"][0]).dtype,

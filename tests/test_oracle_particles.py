@@ -192,3 +192,61 @@ def test_galilean_drift_and_midpoint_current(order):
         assert abs(np.sum(X[a] * J[a]) * dV - np.sum(sp["q"] * sp["w"] * v * mid)) < 1e-12
         # rho^{n+1} sits at x^{n+1}
         assert abs(np.sum(X[a] * rho) * dV - np.sum(sp["q"] * sp["w"] * out[k])) < 1e-12
+
+
+def test_cell_offset_split_pins():
+    """FP32-form positions: faces land at offset 0 of their own cell, the last double below the
+    box end stays in the last cell or wraps to cell 0 at offset 0 (never offset 1), the offset
+    is in [0, 1), and the join reproduces x to the FP32 rounding of the offset."""
+    N, dx = 512, 0.04
+    faces = np.arange(N) * dx
+    i, f = particles.cell_offset_split(faces, dx, N)
+    t = faces * (1.0 / dx)
+    # the cell is the FP64 form's CIC base node (a face whose product rounds just below the
+    # integer belongs to the cell below); 11 of these 512 faces do, and x / dx would differ on 23
+    base, _ = particles.shape_weights(faces, 1.0 / dx, 1)
+    fixed = (f == 0) & (base % N != i)
+    assert np.array_equal(np.where(fixed, i, base % N), i)
+    assert np.array_equal(i[~fixed], base[~fixed] % N)
+    assert int((base % N != np.arange(N)).sum()) == 11
+    assert np.all((f == 0) | (t != np.round(t)))
+    L = N * dx
+    top = np.nextafter(L, 0.0)
+    i, f = particles.cell_offset_split(np.array([top]), dx, N)
+    # t is within one FP64 ulp of N: either 15 + (1 - tiny) rounding to 1.0f -> (0, 0) wrapped
+    assert (i[0], float(f[0])) in ((0, 0.0), (N - 1, float(np.float32(top * (1.0 / dx) - (N - 1)))))
+    assert float(f[0]) < 1.0
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.0, L, 100000)
+    i, f = particles.cell_offset_split(x, dx, N)
+    assert i.min() >= 0 and i.max() < N
+    assert f.dtype == np.float32 and float(f.min()) >= 0.0 and float(f.max()) < 1.0
+    back = particles.cell_offset_join(i, f, dx)
+    d = np.abs(back - x)
+    d = np.minimum(d, L - d)
+    # FP32 rounding of an offset below 1: at most 2^-25 of a cell, plus the FP64 products
+    assert float(d.max()) <= (2.0 ** -25 + 1e-14) * dx
+    # the cell is the FP64 form's nearest-node cell except where the offset rounded up to 1
+    base = np.floor(x * (1.0 / dx)).astype(np.int64) % N
+    moved = i != base
+    assert np.all(f[moved] == 0) and np.array_equal(i[moved], (base[moved] + 1) % N)
+
+
+def test_cell_offset_split_rounds_up_to_the_next_cell():
+    """An offset that rounds to 1.0 in FP32 moves the particle to offset 0 of the next cell."""
+    dx = 1.0
+    x = np.array([3.0 - 2.0 ** -30, 3.0 - 2.0 ** -20, 7.0 - 2.0 ** -40])
+    i, f = particles.cell_offset_split(x, dx, 8)
+    assert list(i) == [3, 2, 7]
+    assert float(f[0]) == 0.0 and float(f[2]) == 0.0
+    assert float(f[1]) == float(np.float32(1.0 - 2.0 ** -20))
+    # and at the box end the next cell wraps to 0
+    i, f = particles.cell_offset_split(np.array([8.0 - 2.0 ** -40]), dx, 8)
+    assert int(i[0]) == 0 and float(f[0]) == 0.0
+
+
+def test_linear_cell_is_c_order():
+    shape = (4, 8, 16)
+    ix, iy, iz = np.meshgrid(np.arange(4), np.arange(8), np.arange(16), indexing="ij")
+    lin = particles.linear_cell(ix, iy, iz, shape)
+    assert np.array_equal(lin.ravel(), np.arange(4 * 8 * 16))

@@ -268,6 +268,7 @@ class Context:
                  tile=(8, 8, 8), sort_interval=20, stream=None, precision=PIC_FP64, filter_passes=0,
                  pusher=0, cycle=0):
         self.shape = tuple(int(n) for n in shape)
+        self.dx = tuple(float(d) for d in dx)
         self.ncell = self.shape[0] * self.shape[1] * self.shape[2]
         self.nmode = self.shape[0] * self.shape[1] * (self.shape[2] // 2 + 1)
         self.variant = variant

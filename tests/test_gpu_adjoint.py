@@ -87,7 +87,7 @@ def _forward_cells(run, sp, E0, B0, A, profile, du=None, margins=False):
         s.uz += du[2]
     rho = torch.empty_like(E[0])
     ctx.deposit_rho([s], rho)
-    dx = run.dx
+    dx = ctx.dx
     L = [ctx.shape[a] * dx[a] for a in range(3)]
     cells = []
     near = torch.full_like(s.x, 1.0)

@@ -69,10 +69,13 @@ def test_reference_arm_line_on_rank_zero():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["warmup"] >= 3
-    assert d["config"] == {"workload": "laser_wakefield", "grid": [128, 128, 512], "particles": 16777216,
-                           "form": "fp32", "shape_order": 3, "centering_order": [8, 8, 16], "variant": 0,
-                           "parallelism": "single"}
+    cfg = dict(d["config"])
+    cfg.pop("note")
+    assert cfg == {"workload": "beam_wakefield", "grid": [256, 256, 1024], "particles": 68108864,
+                   "form": "fp64", "shape_order": 3, "centering_order": [8, 8, 16], "variant": 2,
+                   "parallelism": "single"}
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
 
 

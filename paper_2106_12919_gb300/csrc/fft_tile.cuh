@@ -1,0 +1,146 @@
+// Shared-memory Stockham FFT building blocks (radix 8, plus one radix-4 or radix-2 pass), used by
+// the transform kernels (fft.cu) and by the fused spectral step (psatd.cu).  All sizes are powers
+// of two: index arithmetic uses shifts and masks (lg* = log2).
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic_fft {
+
+constexpr int kZPadShift = 4;  // z-pass lines padded one slot per 16 elements (measured best of 4..32)
+
+// All sizes are powers of two: index arithmetic uses shifts and masks (lg* = log2).
+__device__ __forceinline__ int lg2(int v) { return __ffs(v) - 1; }
+
+struct LayLine {  // z pass: element e of line l at l * LP + e + e / 16
+  int LP;
+  __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + (e >> kZPadShift); }
+  // butterfly b of nb = 2^lgnb per line -> line l, index j
+  __device__ __forceinline__ void map(int b, int lgnb, int& l, int& j) const {
+    l = b >> lgnb;
+    j = b & ((1 << lgnb) - 1);
+  }
+};
+
+struct LayCol {  // y / x pass: element e of column w at e * W + w, W = 2^lgW
+  int lgW;
+  __device__ __forceinline__ int idx(int e, int w) const { return (e << lgW) + w; }
+  __device__ __forceinline__ void map(int b, int lgnb, int& l, int& j) const {
+    j = b >> lgW;
+    l = b & ((1 << lgW) - 1);
+  }
+};
+
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, class C>
+__device__ __forceinline__ C rot90(C a) {
+  C r;
+  if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+
+template <bool INV, class C>
+__device__ __forceinline__ void dft4(C& y0, C& y1, C& y2, C& y3) {
+  C t0 = cadd(y0, y2), t1 = csub(y0, y2);
+  C t2 = cadd(y1, y3), t3 = rot90<INV>(csub(y1, y3));
+  y0 = cadd(t0, t2);
+  y2 = csub(t0, t2);
+  y1 = cadd(t1, t3);
+  y3 = csub(t1, t3);
+}
+
+template <int R, bool INV, class C>
+__device__ __forceinline__ void dft(C* v) {
+  using T = decltype(v[0].x);
+  if (R == 2) {
+    C a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  } else if (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else {  // R == 8: radix-2 split over n and n+4, then two radix-4 DFTs
+    const T r2 = (T)0.70710678118654752440;
+    C b[4], c[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      b[n] = cadd(v[n], v[n + 4]);
+      c[n] = csub(v[n], v[n + 4]);
+    }
+    // c_n *= w8^n, w8 = exp(-+ 2 pi i / 8)
+    C c1 = c[1], c3 = c[3];
+    if (INV) {
+      c[1].x = (c1.x - c1.y) * r2; c[1].y = (c1.x + c1.y) * r2;
+      c[3].x = (-c3.x - c3.y) * r2; c[3].y = (c3.x - c3.y) * r2;
+    } else {
+      c[1].x = (c1.x + c1.y) * r2; c[1].y = (c1.y - c1.x) * r2;
+      c[3].x = (c3.y - c3.x) * r2; c[3].y = (-c3.x - c3.y) * r2;
+    }
+    c[2] = rot90<INV>(c[2]);
+    dft4<INV>(b[0], b[1], b[2], b[3]);
+    dft4<INV>(c[0], c[1], c[2], c[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = b[k];
+      v[2 * k + 1] = c[k];
+    }
+  }
+}
+
+// One Stockham pass of radix R on all lines of the tile, in place.  The CTA has
+// exactly L * N / 8 threads; each thread handles 8 / R butterflies.
+template <int R, bool INV, class C, class LAY>
+__device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int lgN, int lgNs, const C* __restrict__ tw,
+                                              int twstride) {
+  constexpr int PER = 8 / R;
+  constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  const int T = blockDim.x;
+  const int lgnb = lgN - LGR;
+  const int nb = 1 << lgnb, Ns = 1 << lgNs;
+  C v[PER][R];
+  int ol[PER], oj[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    int b = threadIdx.x + q * T;
+    int l, j;
+    lay.map(b, lgnb, l, j);
+    ol[q] = l;
+    oj[q] = j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q][r] = s[lay.idx(j + r * nb, l)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = oj[q], l = ol[q];
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      const int step = k << (lgN - lgNs - LGR);  // (N / (Ns R)) k
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = __ldg(&tw[step * r * twstride]);
+        if (INV) w.y = -w.y;
+        v[q][r] = cmul(v[q][r], w);
+      }
+    }
+    dft<R, INV>(v[q]);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[lay.idx(base + r * Ns, l)] = v[q][r];
+  }
+  __syncthreads();
+}
+
+template <bool INV, class C, class LAY>
+__device__ void fft_tile(C* s, const LAY& lay, int N, const C* __restrict__ tw, int twstride) {
+  const int lgN = lg2(N);
+  int lgNs = 0, rem = lgN;
+  while (rem >= 3) {
+    stockham_pass<8, INV>(s, lay, lgN, lgNs, tw, twstride);
+    lgNs += 3;
+    rem -= 3;
+  }
+  if (rem == 2) stockham_pass<4, INV>(s, lay, lgN, lgNs, tw, twstride);
+  else if (rem == 1) stockham_pass<2, INV>(s, lay, lgN, lgNs, tw, twstride);
+}
+
+}  // namespace pic_fft

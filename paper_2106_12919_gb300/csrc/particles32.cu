@@ -419,6 +419,7 @@ struct TileArgs {
   int wplane, wcomp;      // deposit window plane and component strides (words)
   int G[3];               // gather window edge = T + 3: nodes [T0 - 1, T0 + T + 2)
   int gplane, gcomp;      // gather window plane and component strides (words)
+  int vec_flush;          // flush by aligned groups of 4 z nodes (16-byte vector reductions)
 };
 
 // threads per chunk CTA: 64 registers each, 4 CTAs per SM (256 threads measured 7% faster than 128)
@@ -655,6 +656,33 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
 #pragma unroll
   for (int c = 0; c < 4; ++c) inv[c] = 1.0f / scale[c];
   const int W1 = t.W[1], W2 = t.W[2];
+  if (t.vec_flush) {
+    // Window rows along z cover nodes [T0 - 2, T0 + T + 3); they are flushed as the aligned groups
+    // of 4 nodes starting at T0 - 4 (T0 and Nz are multiples of 4, so a group never wraps), one
+    // 16-byte vector reduction per group and component, nodes outside the window adding 0, groups
+    // whose four sums are all 0 skipped: about a third of the scalar reductions.
+    const int nq = (t.T[2] + 8) >> 2;
+    const int vol4 = t.W[0] * W1 * nq;
+    for (int e = threadIdx.x; e < vol4; e += blockDim.x) {
+      const int g = e % nq, r = e / nq;
+      const int j = r % W1, i = r / W1;
+      const int k0 = 4 * g - 2;  // window index of the group's first node
+      const int o = (((win.org[0] + i) & a.mask[0]) * (int)a.Ny + ((win.org[1] + j) & a.mask[1])) * (int)a.Nz +
+                    ((win.org[2] + k0) & a.mask[2]);
+      const int d = i * t.wplane + j * W2 + k0;
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        int iv[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) iv[l] = (k0 + l >= 0 && k0 + l < W2) ? win.acc[qq * t.wcomp + d + l] : 0;
+        if ((iv[0] | iv[1] | iv[2] | iv[3]) != 0)
+          atomicAdd(reinterpret_cast<float4*>(dst[qq] + o),
+                    make_float4((float)iv[0] * inv[qq], (float)iv[1] * inv[qq], (float)iv[2] * inv[qq],
+                                (float)iv[3] * inv[qq]));
+      }
+    }
+    return;
+  }
   const int vol = t.W[0] * W1 * W2;
   for (int e = threadIdx.x; e < vol; e += blockDim.x) {
     const int k = e % W2, r = e / W2;
@@ -767,6 +795,10 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
   t.n_tiles = ctx->n_tiles;
   t.outside = ctx->bin_outside;
   const size_t smem = tile_layout(ctx, t);
+  bool aligned = ctx->tile[2] % 4 == 0 && ctx->N[2] % 4 == 0;
+  const float* dsts[4] = {a.J[0], a.J[1], a.J[2], a.rho};
+  for (const float* d : dsts) aligned = aligned && (reinterpret_cast<uintptr_t>(d) % 16 == 0);
+  t.vec_flush = aligned ? 1 : 0;
   // sum over tiles of ceil(count / kTileChunk) < n_tiles + n / kTileChunk: surplus CTAs return at once
   const unsigned nb = (unsigned)(ctx->n_tiles + (a.n + kTileChunk - 1) / kTileChunk);
   if (smem > 48 * 1024) {

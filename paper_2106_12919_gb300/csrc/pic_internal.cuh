@@ -108,6 +108,13 @@ struct pic_ctx {
   double2* twid[3];  // twiddles exp(-2 pi i j / N_a), j < N_a
   float2* twid32[3]; // the same rounded to FP32
   double2* coef;     // [ncoef][nmode]
+  // Compact copy of the tables read by the step's update (NULL when v_gal has a transverse
+  // component): the coefficients depend on k_x, k_y through [k_x]_s^2, [k_y]_s^2 only, so the
+  // quarter ix <= Nx/2, iy <= Ny/2 of the (kx, ky) plane holds them all ([ncoef][nqx][nqy][nzh]);
+  // real doubles for the standard variant (every coefficient is real there), double2 otherwise.
+  double* coefq;
+  int coefq_real;
+  int64_t nqx, nqy, nq;
 
   // spectral state and work (paper-convention spectra)
   double2* EBh;      // [6][nmode]: E^x..E^z, B^x..B^z
@@ -205,11 +212,13 @@ using CPtr6 = CP6<double2>;
 // fft.cu ---------------------------------------------------------------------
 pic_status fft_setup(pic_ctx* ctx);
 // Forward R2C of ncomp real arrays into spectral arrays (plain DFT, unnormalised). T = double | float.
+// with_x = false stops after the z and y passes (the fused spectral step does the x pass).
 template <class T>
-pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp);
-// Inverse C2R (unnormalised); spectral arrays are destroyed.
+pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp, bool with_x = true);
+// Inverse C2R (unnormalised); spectral arrays are destroyed.  with_x = false: the input has had its
+// x pass already (the fused spectral step), only the y and z passes run.
 template <class T>
-pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp);
+pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp, bool with_x = true);
 
 // psatd.cu -------------------------------------------------------------------
 long double fornberg_alpha_s(int m, int n);  // alpha^s_{m,n} (Eq. eq_Fornberg_staggered), host
@@ -229,6 +238,14 @@ pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, 
                        double scale);
 // G[c] = Z_c * src[c] * scale, src = the six E,B spectra given (paper convention) -> nodal DFT.
 pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale);
+// Fused spectral step of the hybrid (and nodal) cycle: the x pass of the forward transforms of
+// J (3) and rho^{n+1} (J[c], rp hold them after the z and y passes), the update of every mode
+// (as psatd_update with g_mode 0, j_yee 0, the filter when the context has one), and the x pass of
+// the inverse transforms of the six G spectra, per column tile in shared memory.  On return: EB
+// updated, rp fully transformed (rho^{n+1} for the next step), J the Yee-centered spectrum if
+// write_j, G ready for the inverse y and z passes.  C = double2 | float2.
+template <class C>
+pic_status psatd_fused_step(pic_ctx* ctx, C* EB, C* J, const C* rn, C* rp, C* G, int write_j);
 // FP32-form counterparts (FP32 spectra, FP64 tables rounded at use).
 pic_status psatd_update32(pic_ctx* ctx, float2* EB, float2* J, const float2* rn, const float2* rp, float2* G,
                           int g_mode, int j_yee, int write_j, int smooth);
@@ -273,6 +290,38 @@ __device__ __forceinline__ void vay_push(T& ux, T& uy, T& uz, const T* f, T k, T
   ux = sn * (upx + ut * qx + (upy * qz - upz * qy));
   uy = sn * (upy + ut * qy + (upz * qx - upx * qz));
   uz = sn * (upz + ut * qz + (upx * qy - upy * qx));
+}
+
+// Read access to the update's coefficient tables: the compact quarter tables when the context has
+// them, else the full [ncoef][nmode] tables.
+struct CoefView {
+  const double* q;       // compact tables (NULL: use full)
+  const double2* full;   // full tables
+  int real;              // compact tables hold real doubles
+  int64_t nqy, nq, nmode;
+  int nx, ny;            // grid sizes of the two folded axes
+  __device__ __forceinline__ int64_t index(uint32_t ix, uint32_t iy, uint32_t iz, int64_t nzh) const {
+    const uint32_t qx = min(ix, (uint32_t)nx - ix), qy = min(iy, (uint32_t)ny - iy);
+    return ((int64_t)qx * nqy + qy) * nzh + iz;
+  }
+  // coefficient k of mode m = (ix, iy, iz), in FP64
+  __device__ __forceinline__ double2 get(int k, int64_t m, int64_t qidx) const {
+    if (q == nullptr) return __ldg(full + k * nmode + m);
+    if (real) return make_double2(__ldg(q + k * nq + qidx), 0.0);
+    return __ldg(reinterpret_cast<const double2*>(q) + k * nq + qidx);
+  }
+};
+inline CoefView coef_view(const pic_ctx* ctx) {
+  CoefView v;
+  v.q = ctx->coefq;
+  v.full = ctx->coef;
+  v.real = ctx->coefq_real;
+  v.nqy = ctx->nqy;
+  v.nq = ctx->nq;
+  v.nmode = ctx->nmode;
+  v.nx = (int)ctx->N[0];
+  v.ny = (int)ctx->N[1];
+  return v;
 }
 
 // index of a coefficient table by name ("TC", "TS", ..., see pic_coefficient), -1 if unknown

@@ -17,6 +17,7 @@
 // of modest frequency, so the rule is exact to rounding).  a = 0 uses the
 // standard forms (Sec. 4.2) directly.
 #include "pic_internal.cuh"
+#include "fft_tile.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -245,6 +246,28 @@ __global__ void build_tables_kernel(TableArgs t) {
   for (int k = 0; k < t.ncoef; ++k) t.coef[k * t.nmode + m] = cf.v[k];
 }
 
+// Compact tables: entry (qx, qy, iz) of the quarter qx <= Nx/2, qy <= Ny/2 is the full table's mode
+// (qx, qy, iz); the update reads it for the four modes (+-kx, +-ky, kz).
+struct CompactArgs {
+  const double2* full;
+  double* q;
+  int real, ncoef;
+  int64_t Ny, nzh, nqy, nq, nmode;
+};
+
+__global__ void compact_tables_kernel(CompactArgs c) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= c.nq) return;
+  const int64_t iz = e % c.nzh, r = e / c.nzh;
+  const int64_t qy = r % c.nqy, qx = r / c.nqy;
+  const int64_t m = (qx * c.Ny + qy) * c.nzh + iz;
+  for (int k = 0; k < c.ncoef; ++k) {
+    const double2 v = c.full[k * c.nmode + m];
+    if (c.real) c.q[k * c.nq + e] = v.x;
+    else reinterpret_cast<double2*>(c.q)[k * c.nq + e] = v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // fused update
 // ---------------------------------------------------------------------------
@@ -254,7 +277,7 @@ struct UpdArgs {
   C* J;                 // [3][nmode] in: DFT of the nodal (or Yee, j_yee) deposit; out: Yee-centered
   const C* rn;          // rho^n
   const C* rp;          // rho^{n+1}
-  const double2* coef;  // [ncoef][nmode], FP64 in every form
+  CoefView coef;        // FP64 in every form
   C* G;                 // [6][nmode] out
   // 1D tables in the data precision (the FP32 form reads FP32 copies of them: converting FP64
   // values per mode would run on this part's slow FP64 pipe)
@@ -271,26 +294,19 @@ struct UpdArgs {
   int write_j;  // write the Yee-centered J back
 };
 
-// Fused k-space update of one mode per thread.  The FP64 coefficient tables are
-// read in FP64 and rounded to the data precision at use.
+// The k-space update of one mode (Secs. 4.2-4.4): E, B in and out (paper-convention spectra),
+// J in (the DFT of the nodal deposit, or with j_yee the Yee-centered spectrum) and out (Yee-centered,
+// after the optional filter), rho^n, rho^{n+1}; G[6] out = the fields the next gather reads (E, B or
+// <E>, <B>) times the centering symbols (g_mode 0) or the half-cell shifts back to the Yee DFT
+// (g_mode 1), times gscale.  The FP64 coefficient tables are read in FP64 and rounded to the data
+// precision at use.
 template <int VAR, class C>
-__global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
+__device__ __forceinline__ void mode_update(const UpdArgs<C>& u, uint32_t ix, uint32_t iy, uint32_t iz, int64_t m,
+                                            C (&E)[3], C (&B)[3], C (&J)[3], C rn, C rp, C (&G)[6]) {
   using T = decltype(C().x);
-  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (m >= u.nmode) return;
-  const int64_t nm = u.nmode;
-  const int64_t iz = m % u.nzh, r = m / u.nzh;
-  const int64_t iy = r % u.Ny, ix = r / u.Ny;
+  const int64_t qidx = u.coef.index(ix, iy, iz, u.nzh);
   const T k[3] = {(T)u.ks[0][ix], (T)u.ks[1][iy], (T)u.ks[2][iz]};
   const T zx = (T)u.zt[0][ix], zy = (T)u.zt[1][iy], zz = (T)u.zt[2][iz];
-  C E[3], B[3], J[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    E[a] = u.EB[a * nm + m];
-    B[a] = u.EB[(3 + a) * nm + m];
-    J[a] = u.J[a * nm + m];
-  }
-  C rn = u.rn[m], rp = u.rp[m];
   if (!u.j_yee) {
     J[0] = cscale(J[0], zx);
     J[1] = cscale(J[1], zy);
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
   cross(E, kE);
   cross(B, kB);
   cross(J, kJ);
-  auto co = [&](int idx) { return cast_c<C>(__ldg(u.coef + idx * nm + m)); };
+  auto co = [&](int idx) { return cast_c<C>(u.coef.get(idx, m, qidx)); };
   const C TC = co(COEF_TC), TS = co(COEF_TS), X1 = co(COEF_X1), X2 = co(COEF_X2), TX3 = co(COEF_TX3),
           X4 = co(COEF_X4);
   const T c2 = (T)u.c2;
@@ -351,29 +367,148 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    u.EB[a * nm + m] = En[a];
-    u.EB[(3 + a) * nm + m] = Bn[a];
+    E[a] = En[a];
+    B[a] = Bn[a];
+  }
+  const T s = (T)u.gscale;
+  if (u.g_mode == 0) {
+    G[0] = cscale(Ga[0], zx * s);
+    G[1] = cscale(Ga[1], zy * s);
+    G[2] = cscale(Ga[2], zz * s);
+    G[3] = cscale(Gb[0], zy * zz * s);
+    G[4] = cscale(Gb[1], zx * zz * s);
+    G[5] = cscale(Gb[2], zx * zy * s);
+  } else {
+    const C hx = cconj(u.hs[0][ix]), hy = cconj(u.hs[1][iy]), hz = cconj(u.hs[2][iz]);
+    G[0] = cscale(cmul(Ga[0], hx), s);
+    G[1] = cscale(cmul(Ga[1], hy), s);
+    G[2] = cscale(cmul(Ga[2], hz), s);
+    G[3] = cscale(cmul(Gb[0], cmul(hy, hz)), s);
+    G[4] = cscale(cmul(Gb[1], cmul(hx, hz)), s);
+    G[5] = cscale(cmul(Gb[2], cmul(hx, hy)), s);
+  }
+}
+
+// One mode per thread over the whole spectrum.
+template <int VAR, class C>
+__global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= u.nmode) return;
+  const int64_t nm = u.nmode;
+  uint32_t ix, iy, iz;
+  mode_xyz(m, (uint32_t)u.nzh, __ffsll(u.Ny) - 1, ix, iy, iz);
+  C E[3], B[3], J[3], G[6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    E[a] = u.EB[a * nm + m];
+    B[a] = u.EB[(3 + a) * nm + m];
+    J[a] = u.J[a * nm + m];
+  }
+  mode_update<VAR>(u, ix, iy, iz, m, E, B, J, u.rn[m], u.rp[m], G);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u.EB[a * nm + m] = E[a];
+    u.EB[(3 + a) * nm + m] = B[a];
   }
   if (u.write_j) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) u.J[a * nm + m] = J[a];
   }
-  const T s = (T)u.gscale;
-  if (u.g_mode == 0) {
-    u.G[0 * nm + m] = cscale(Ga[0], zx * s);
-    u.G[1 * nm + m] = cscale(Ga[1], zy * s);
-    u.G[2 * nm + m] = cscale(Ga[2], zz * s);
-    u.G[3 * nm + m] = cscale(Gb[0], zy * zz * s);
-    u.G[4 * nm + m] = cscale(Gb[1], zx * zz * s);
-    u.G[5 * nm + m] = cscale(Gb[2], zx * zy * s);
-  } else {
-    const C hx = cconj(u.hs[0][ix]), hy = cconj(u.hs[1][iy]), hz = cconj(u.hs[2][iz]);
-    u.G[0 * nm + m] = cscale(cmul(Ga[0], hx), s);
-    u.G[1 * nm + m] = cscale(cmul(Ga[1], hy), s);
-    u.G[2 * nm + m] = cscale(cmul(Ga[2], hz), s);
-    u.G[3 * nm + m] = cscale(cmul(Gb[0], cmul(hy, hz)), s);
-    u.G[4 * nm + m] = cscale(cmul(Gb[1], cmul(hx, hz)), s);
-    u.G[5 * nm + m] = cscale(cmul(Gb[2], cmul(hx, hy)), s);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) u.G[c * nm + m] = G[c];
+}
+
+// Fused spectral step: one CTA per (k_y, tile of W consecutive k_z columns), all Nx values of k_x.
+// Shared memory holds three pair buffers of [Nx][2W] complex values (element e of column w at
+// e * 2W + w): first the x-pass inputs J_x, J_y | J_z, rho^{n+1} (after their z and y passes),
+// transformed forward along x in place; then, mode by mode, the update reads J and rho^{n+1} from
+// them and writes the six G values over them (G_0, G_1 | G_2, G_3 | G_4, G_5; each mode's slots are
+// read before they are written, by the same thread), and the three buffers are transformed back
+// along x.  The CTA has Nx * W / 4 threads (8 elements of a pair buffer per thread in a pass).
+// Launch order pairs k_y and Ny - k_y (blockIdx.x = 2 q or 2 q + 1), so the two CTAs that read the
+// same compact-table entries run side by side.
+template <class C>
+struct FusedArgs {
+  UpdArgs<C> u;
+  const C* twx;  // x-axis twiddles exp(-2 pi i j / Nx)
+  int Nx, W;
+};
+
+template <int VAR, class C, int MINB>
+__global__ void __launch_bounds__(256, MINB) fused_step_kernel(FusedArgs<C> f) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const UpdArgs<C>& u = f.u;
+  const int Nx = f.Nx, W = f.W, W2 = 2 * W;
+  const int lgW = pic_fft::lg2(W), lgNx = pic_fft::lg2(Nx);
+  const int Ny = (int)u.Ny, nzh = (int)u.nzh;
+  const int b = blockIdx.x;
+  const int ky = (b & 1) ? Ny - ((b + 1) >> 1) : (b >> 1);
+  const int col0 = blockIdx.y * W;
+  const int wv = min(W, nzh - col0);
+  const int64_t nm = u.nmode;
+  const int64_t xs = (int64_t)Ny * nzh;           // stride between k_x rows
+  const int64_t base = (int64_t)ky * nzh + col0;  // mode (0, ky, col0)
+  const int per = Nx * W;                         // elements of one set
+  C* const P0 = sm;
+  C* const P1 = sm + 2 * per;
+  C* const P2 = sm + 4 * per;
+  // 1. the x-pass inputs: set s -> buffer s / 2 (at sm + s / 2 * 2 per), columns (s % 2) W + w
+  for (int t = threadIdx.x; t < 4 * per; t += blockDim.x) {
+    const int s = t >> (lgNx + lgW), r = t & (per - 1);
+    const int e = r >> lgW, w = r & (W - 1);
+    const C* src = s < 3 ? u.J + s * nm : u.rp;
+    sm[(s >> 1) * 2 * per + e * W2 + (s & 1) * W + w] = w < wv ? src[base + e * xs + w] : czero<C>();
+  }
+  __syncthreads();
+  const pic_fft::LayCol lay{lgW + 1};
+  pic_fft::fft_tile<false>(P0, lay, Nx, f.twx, 1);
+  pic_fft::fft_tile<false>(P1, lay, Nx, f.twx, 1);
+  // 2. the update of every mode of the tile
+  for (int t = threadIdx.x; t < per; t += blockDim.x) {
+    const int e = t >> lgW, w = t & (W - 1);
+    const int i0 = e * W2 + w, i1 = i0 + W;
+    C G[6];
+    if (w < wv) {
+      const int64_t m = base + e * xs + w;
+      C E[3], B[3], J[3] = {P0[i0], P0[i1], P1[i0]};
+      const C rp = P1[i1];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        E[a] = u.EB[a * nm + m];
+        B[a] = u.EB[(3 + a) * nm + m];
+      }
+      const_cast<C*>(u.rp)[m] = rp;  // rho^{n+1}, fully transformed: the next step's rho^n
+      mode_update<VAR>(u, (uint32_t)e, (uint32_t)ky, (uint32_t)(col0 + w), m, E, B, J, u.rn[m], rp, G);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        u.EB[a * nm + m] = E[a];
+        u.EB[(3 + a) * nm + m] = B[a];
+      }
+      if (u.write_j) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u.J[a * nm + m] = J[a];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) G[c] = czero<C>();
+    }
+    P0[i0] = G[0];
+    P0[i1] = G[1];
+    P1[i0] = G[2];
+    P1[i1] = G[3];
+    P2[i0] = G[4];
+    P2[i1] = G[5];
+  }
+  __syncthreads();
+  // 3. the inverse x pass of the six G columns, then out
+  pic_fft::fft_tile<true>(P0, lay, Nx, f.twx, 1);
+  pic_fft::fft_tile<true>(P1, lay, Nx, f.twx, 1);
+  pic_fft::fft_tile<true>(P2, lay, Nx, f.twx, 1);
+  for (int t = threadIdx.x; t < 6 * per; t += blockDim.x) {
+    const int s = t >> (lgNx + lgW), r = t & (per - 1);
+    const int e = r >> lgW, w = r & (W - 1);
+    if (w < wv) u.G[s * nm + base + e * xs + w] = sm[(s >> 1) * 2 * per + e * W2 + (s & 1) * W + w];
   }
 }
 
@@ -702,6 +837,28 @@ pic_status psatd_setup(pic_ctx* ctx) {
   const int bs = 128;
   build_tables_kernel<<<(unsigned)((ctx->nmode + bs - 1) / bs), bs, 0, ctx->stream>>>(t);
   PIC_LAUNCH_CHECK(ctx);
+  // compact tables for the step's update (see pic_ctx::coefq)
+  ctx->coefq = nullptr;
+  if (ctx->variant == PIC_PSATD_STANDARD || (ctx->vg[0] == 0.0 && ctx->vg[1] == 0.0)) {
+    ctx->coefq_real = ctx->variant == PIC_PSATD_STANDARD ? 1 : 0;
+    ctx->nqx = ctx->N[0] / 2 + 1;
+    ctx->nqy = ctx->N[1] / 2 + 1;
+    ctx->nq = ctx->nqx * ctx->nqy * ctx->nzh;
+    const size_t words = (size_t)ctx->ncoef * ctx->nq * (ctx->coefq_real ? 1 : 2);
+    PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->coefq, words * sizeof(double)));
+    CompactArgs c;
+    c.full = ctx->coef;
+    c.q = ctx->coefq;
+    c.real = ctx->coefq_real;
+    c.ncoef = ctx->ncoef;
+    c.Ny = ctx->N[1];
+    c.nzh = ctx->nzh;
+    c.nqy = ctx->nqy;
+    c.nq = ctx->nq;
+    c.nmode = ctx->nmode;
+    compact_tables_kernel<<<(unsigned)((ctx->nq + 255) / 256), 256, 0, ctx->stream>>>(c);
+    PIC_LAUNCH_CHECK(ctx);
+  }
   PIC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return PIC_OK;
 }
@@ -736,7 +893,7 @@ pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C
   u.J = J;
   u.rn = rn;
   u.rp = rp;
-  u.coef = ctx->coef;
+  u.coef = coef_view(ctx);
   u.G = G;
   for (int a = 0; a < 3; ++a) {
     tab1d(ctx, a, &u.ks[a], &u.zt[a], &u.flt[a], &u.hs[a]);
@@ -759,6 +916,56 @@ pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
+
+static const double2* x_twiddles(const pic_ctx* ctx, double2*) { return ctx->twid[0]; }
+static const float2* x_twiddles(const pic_ctx* ctx, float2*) { return ctx->twid32[0]; }
+
+template <class C>
+pic_status psatd_fused_step(pic_ctx* ctx, C* EB, C* J, const C* rn, C* rp, C* G, int write_j) {
+  FusedArgs<C> f;
+  UpdArgs<C>& u = f.u;
+  u.EB = EB;
+  u.J = J;
+  u.rn = rn;
+  u.rp = rp;
+  u.coef = coef_view(ctx);
+  u.G = G;
+  for (int a = 0; a < 3; ++a) {
+    tab1d(ctx, a, &u.ks[a], &u.zt[a], &u.flt[a], &u.hs[a]);
+    if (ctx->filter_passes <= 0) u.flt[a] = nullptr;
+  }
+  u.Ny = ctx->N[1];
+  u.nzh = ctx->nzh;
+  u.nmode = ctx->nmode;
+  u.c2 = ctx->c * ctx->c;
+  u.gscale = 1.0 / (double)ctx->ncell;
+  u.g_mode = 0;
+  u.j_yee = 0;
+  u.write_j = write_j;
+  const int Nx = (int)ctx->N[0];
+  f.Nx = Nx;
+  f.W = std::min(16, 1024 / Nx);  // Nx * W <= 1024: at most 256 threads, 6 Nx W elements of shared memory
+  f.twx = x_twiddles(ctx, (C*)nullptr);
+  const int threads = Nx * f.W / 4;
+  const size_t smem = (size_t)6 * Nx * f.W * sizeof(C);
+  dim3 grid((unsigned)ctx->N[1], (unsigned)((ctx->nzh + f.W - 1) / f.W));
+  constexpr int minb = sizeof(C) == 8 ? 2 : 1;
+  const bool avg = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN;
+  if (avg) {
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fused_step_kernel<2, C, minb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    fused_step_kernel<2, C, minb><<<grid, threads, smem, ctx->stream>>>(f);
+  } else {
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fused_step_kernel<0, C, minb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    fused_step_kernel<0, C, minb><<<grid, threads, smem, ctx->stream>>>(f);
+  }
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
+
+template pic_status psatd_fused_step<double2>(pic_ctx*, double2*, double2*, const double2*, double2*, double2*, int);
+template pic_status psatd_fused_step<float2>(pic_ctx*, float2*, float2*, const float2*, float2*, float2*, int);
 
 pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
                            int write_j, int smooth) {

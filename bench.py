@@ -274,7 +274,7 @@ def cufft_reference(shape, dtype, libpic_ms):
             "note": "cuFFT via torch.fft: 4 R2C + 6 C2R 3D transforms of the grid per step, reference only"}
 
 
-def setup_form(form, w, stream):
+def setup_form(form, w, stream, tile=(8, 8, 8)):
     """Context and device state of one form on the workload (inputs resident in HBM)."""
     import torch
     from paper_2106_12919_gb300 import pic
@@ -282,7 +282,7 @@ def setup_form(form, w, stream):
     ncell = int(np.prod(p["shape"]))
     fp32 = form == "fp32"
     ctx = pic.Context(p["shape"], p["dx"], p["dt"], p["shape_order"], p["centering_order"], p["variant"], p["v_gal"],
-                      p["spectral_order"], p["c"], p["eps0"], stream=stream,
+                      p["spectral_order"], p["c"], p["eps0"], stream=stream, tile=tuple(tile),
                       precision=pic.PIC_FP32 if fp32 else pic.PIC_FP64)
     tdt = torch.float32 if fp32 else torch.float64
     with torch.cuda.stream(stream):
@@ -470,7 +470,7 @@ def run_form(form, w, args, world, rank, local, full=True):
     ncell = int(np.prod(p["shape"]))
     fp32 = form == "fp32"
     stream = torch.cuda.Stream()
-    ctx, E, B, J, rho, sp = setup_form(form, w, stream)
+    ctx, E, B, J, rho, sp = setup_form(form, w, stream, args.tile)
     npart = sum(s.n for s in sp)
     step = ctx.step32 if fp32 else ctx.step
     (ctx.deposit_rho32 if fp32 else ctx.deposit_rho)(sp, rho)
@@ -560,6 +560,8 @@ def main():
                     help="end-to-end loop with direct pic_step calls instead of their CUDA graphs")
     ap.add_argument("--form", default="both", choices=["both", "fp32", "fp64"],
                     help="both: FP32 form timed as the headline, FP64 form beside it")
+    ap.add_argument("--tile", type=int, nargs=3, default=(8, 8, 8), metavar=("TX", "TY", "TZ"),
+                    help="particle tile edge in cells (pic_ext.tile)")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                     help="run the workload's generator on a smaller box (same dx, dt, physics), e.g. for profiling")
     args = ap.parse_args()
@@ -593,6 +595,7 @@ def main():
     config = workload_config(args.workload, world, shape)
     config["form"] = forms[0]
     config["particles"] = head["npart"]
+    config["tile"] = list(args.tile)
     config["cache"] = "working set (%.1f GB) > L2 (129 MB); no flush needed" % head["bytes_resident"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

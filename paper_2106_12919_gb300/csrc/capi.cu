@@ -102,17 +102,16 @@ pic_status store_yee(pic_ctx* ctx, const double2* src, const int* kinds, int nco
   return fft_c2r(ctx, g, o, ncomp);
 }
 
-// G (nodal spectra, already scaled) -> ctx->nodal real arrays; with_x = false when the fused
-// spectral step has done the x pass already.
-pic_status g_to_nodal(pic_ctx* ctx, bool with_x = true) {
+// G (nodal spectra, already scaled) -> ctx->nodal real arrays.
+pic_status g_to_nodal(pic_ctx* ctx) {
   CPtr6 g;
   RPtr6 o;
   for (int c = 0; c < 6; ++c) {
     g.p[c] = ctx->G + c * ctx->nmode;
     o.p[c] = ctx->nodal + c * ctx->ncell;
   }
-  StageScope t(ctx, STAGE_FFT, with_x ? 3 : 2);
-  return fft_c2r(ctx, g, o, 6, with_x);
+  StageScope t(ctx, STAGE_FFT, 3);
+  return fft_c2r(ctx, g, o, 6);
 }
 
 }  // namespace
@@ -505,11 +504,9 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
     }
     in.p[3] = rho;
     out.p[3] = ctx->rhoh[1 - cur];
-    // hybrid and nodal cycles: the x passes of both transforms run inside the fused spectral step
-    const bool fused = !stag;
     {
-      StageScope t(ctx, STAGE_FFT, fused ? 2 : 3);
-      PIC_TRY(fft_r2c(ctx, in, out, 4, !fused));
+      StageScope t(ctx, STAGE_FFT, 3);
+      PIC_TRY(fft_r2c(ctx, in, out, 4));
     }
     if (stag) {
       // J was deposited at its Yee positions: plain DFT -> paper convention, in place
@@ -518,17 +515,14 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
       StageScope t(ctx, STAGE_OTHER, 1);
       PIC_TRY(psatd_phase(ctx, jh, jh, kKindJ, 3, -1, 1.0));
     }
-    if (fused) {
+    {
+      // hybrid: J nodal (centered in the update), G = nodal E, B; staggered: J and G on the Yee grid
       StageScope t(ctx, STAGE_UPDATE, 1);
-      PIC_TRY(psatd_fused_step<double2>(ctx, ctx->EBh, ctx->Jh, ctx->rhoh[cur], ctx->rhoh[1 - cur], ctx->G,
-                                        (last && J) ? 1 : 0));
-    } else {
-      // staggered: J and G on the Yee grid
-      StageScope t(ctx, STAGE_UPDATE, 1);
-      PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], 1, 1, (last && J) ? 1 : 0, 1));
+      PIC_TRY(psatd_update_ex(ctx, ctx->rhoh[cur], ctx->rhoh[1 - cur], stag ? 1 : 0, stag ? 1 : 0,
+                              (last && J) ? 1 : 0, 1));
     }
     cur = 1 - cur;
-    if (!last) PIC_TRY(g_to_nodal(ctx, !fused));
+    if (!last) PIC_TRY(g_to_nodal(ctx));
     ++ctx->steps_done;
   }
   // exit: Yee E, B and J

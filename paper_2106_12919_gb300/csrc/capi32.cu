@@ -88,16 +88,15 @@ pic_status store_yee32(pic_ctx* ctx, const float2* src, const int* kinds, int nc
   return fft_c2r<float>(ctx, g, o, ncomp);
 }
 
-// G -> nodal E, B; with_x = false when the fused spectral step has done the x pass already.
-pic_status g_to_nodal32(pic_ctx* ctx, bool with_x = true) {
+pic_status g_to_nodal32(pic_ctx* ctx) {
   CP6<float2> g;
   RP6<float> o;
   for (int c = 0; c < 6; ++c) {
     g.p[c] = Gs(ctx) + c * ctx->nmode;
     o.p[c] = nodal(ctx) + c * ctx->ncell;
   }
-  StageScope t(ctx, STAGE_FFT, with_x ? 3 : 2);
-  return fft_c2r<float>(ctx, g, o, 6, with_x);
+  StageScope t(ctx, STAGE_FFT, 3);
+  return fft_c2r<float>(ctx, g, o, 6);
 }
 
 }  // namespace
@@ -238,7 +237,7 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
       st = particles_bin32_decide(ctx, total, 1);
     }
     if (st == PIC_OK) {
-      StageScope t(ctx, STAGE_BIN, sp[0].n > 0 ? 12 : 9);
+      StageScope t(ctx, STAGE_BIN, bin32_launches(ctx, sp[0].n, true, false));
       st = particles_bin32(ctx, &sp[0], ctx->sp_off[0], ctx->bin_gate, ctx->sp_chunk[0], false);
     }
     ctx->stream = main_stream;
@@ -301,12 +300,12 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
         if (s == 0 && q == 0 && early_bin) {
           PIC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));  // binned on the second stream
         } else {
-          StageScope t(ctx, STAGE_BIN, sp[q].n > 0 ? 12 : 9);
+          StageScope t(ctx, STAGE_BIN, bin32_launches(ctx, sp[q].n, true, false));
           PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q], false));
         }
         StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
         PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q], ctx->sp_chunk[q],
-                                         bin32_scatter_gate(ctx)));
+                                         bin32_two_level(ctx) ? nullptr : bin32_scatter_gate(ctx)));
       } else {
         StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
         PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
@@ -339,11 +338,9 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     }
     in.p[3] = rho;
     out.p[3] = rhoh(ctx, 1 - cur);
-    // hybrid and nodal cycles: the x passes of both transforms run inside the fused spectral step
-    const bool fused = !stag;
     {
-      StageScope t(ctx, STAGE_FFT, fused ? 2 : 3);
-      PIC_TRY32(fft_r2c<float>(ctx, in, out, 4, !fused));
+      StageScope t(ctx, STAGE_FFT, 3);
+      PIC_TRY32(fft_r2c<float>(ctx, in, out, 4));
     }
     if (stag) {
       // J was deposited at its Yee positions: plain DFT -> paper convention, in place
@@ -352,18 +349,14 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
       StageScope t(ctx, STAGE_OTHER, 1);
       PIC_TRY32(psatd_phase32(ctx, jh, jh, kKindJ, 3, -1, 1.0));
     }
-    if (fused) {
+    {
+      // hybrid: J nodal (centered in the update), G = nodal E, B; staggered: J and G on the Yee grid
       StageScope t(ctx, STAGE_UPDATE, 1);
-      PIC_TRY32(psatd_fused_step<float2>(ctx, EBh(ctx), Jh(ctx), rhoh(ctx, cur), rhoh(ctx, 1 - cur), Gs(ctx),
-                                         (last && J) ? 1 : 0));
-    } else {
-      // staggered: J and G on the Yee grid
-      StageScope t(ctx, STAGE_UPDATE, 1);
-      PIC_TRY32(psatd_update32(ctx, EBh(ctx), Jh(ctx), rhoh(ctx, cur), rhoh(ctx, 1 - cur), Gs(ctx), 1, 1,
-                               (last && J) ? 1 : 0, 1));
+      PIC_TRY32(psatd_update32(ctx, EBh(ctx), Jh(ctx), rhoh(ctx, cur), rhoh(ctx, 1 - cur), Gs(ctx), stag ? 1 : 0,
+                               stag ? 1 : 0, (last && J) ? 1 : 0, 1));
     }
     cur = 1 - cur;
-    if (!last) PIC_TRY32(g_to_nodal32(ctx, !fused));
+    if (!last) PIC_TRY32(g_to_nodal32(ctx));
     ++ctx->steps_done;
   }
   if (fd) return PIC_OK;

@@ -280,7 +280,7 @@ pic_status fft_setup(pic_ctx* ctx) {
 }
 
 template <class T>
-pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp, bool with_x) {
+pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp) {
   using C = typename Cplx<T>::type;
   const int Nz = (int)ctx->N[2];
   const int L = z_lines_per_cta(Nz);
@@ -290,14 +290,14 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
   fft_z_r2c_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
-  if (st != PIC_OK || !with_x) return st;
+  if (st != PIC_OK) return st;
   return launch_strided<C>(ctx, out, 0, false, ncomp);
 }
 
 template <class T>
-pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp, bool with_x) {
+pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp) {
   using C = typename Cplx<T>::type;
-  pic_status st = with_x ? launch_strided<C>(ctx, in, 0, true, ncomp) : PIC_OK;
+  pic_status st = launch_strided<C>(ctx, in, 0, true, ncomp);
   if (st != PIC_OK) return st;
   st = launch_strided<C>(ctx, in, 1, true, ncomp);
   if (st != PIC_OK) return st;
@@ -311,7 +311,7 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
   return PIC_OK;
 }
 
-template pic_status fft_r2c<double>(pic_ctx*, CRP6<double>, CP6<double2>, int, bool);
-template pic_status fft_r2c<float>(pic_ctx*, CRP6<float>, CP6<float2>, int, bool);
-template pic_status fft_c2r<double>(pic_ctx*, CP6<double2>, RP6<double>, int, bool);
-template pic_status fft_c2r<float>(pic_ctx*, CP6<float2>, RP6<float>, int, bool);
+template pic_status fft_r2c<double>(pic_ctx*, CRP6<double>, CP6<double2>, int);
+template pic_status fft_r2c<float>(pic_ctx*, CRP6<float>, CP6<float2>, int);
+template pic_status fft_c2r<double>(pic_ctx*, CP6<double2>, RP6<double>, int);
+template pic_status fft_c2r<float>(pic_ctx*, CP6<float2>, RP6<float>, int);

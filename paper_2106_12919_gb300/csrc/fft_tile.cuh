@@ -1,6 +1,6 @@
-// Shared-memory Stockham FFT building blocks (radix 8, plus one radix-4 or radix-2 pass), used by
-// the transform kernels (fft.cu) and by the fused spectral step (psatd.cu).  All sizes are powers
-// of two: index arithmetic uses shifts and masks (lg* = log2).
+// Shared-memory Stockham FFT building blocks (radix 8, plus one radix-4 or radix-2 pass) of the
+// transform kernels (fft.cu).  All sizes are powers of two: index arithmetic uses shifts and masks
+// (lg* = log2).
 #pragma once
 
 #include "pic_internal.cuh"

@@ -865,7 +865,7 @@ __device__ __forceinline__ int key_of(const Key32Args& a, int c) {
   return (t << a.cpt_shift) | local;
 }
 
-__device__ __forceinline__ void key32_one(const Key32Args& a, int64_t p) {
+__device__ __forceinline__ bool key32_one(const Key32Args& a, int64_t p) {
   const int k = key_of(a, a.cell[p]);
   a.key[p] = k;
   const unsigned active = __activemask();
@@ -874,16 +874,29 @@ __device__ __forceinline__ void key32_one(const Key32Args& a, int64_t p) {
   const int lane_id = threadIdx.x & 31;
   const int up = __shfl_up_sync(active, k, 1);
   const int prev = lane_id > 0 ? up : (p > 0 ? key_of(a, a.cell[p - 1]) : k);
-  if (prev > k) *a.unsorted = 1;
   const unsigned peers = __match_any_sync(active, k);
   const int leader = __ffs(peers) - 1;
   if ((int)(threadIdx.x & 31) == leader) atomicAdd(a.counts + k, (uint32_t)__popc(peers));
+  return prev > k;
+}
+
+// "some key is smaller than its predecessor's": one global store per block at most (a store per
+// out-of-order particle to the same word serialises at L2 when many particles moved)
+__device__ __forceinline__ void flag_unsorted(const Key32Args& a, bool mine) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  if (mine) s_any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0 && s_any) *a.unsorted = 1;
 }
 
 __global__ void key32_kernel(Key32Args a) {
   if (gated_off(a.gate)) return;
+  bool mine = false;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x)
-    key32_one(a, p);
+    mine |= key32_one(a, p);
+  flag_unsorted(a, mine);
 }
 
 // exclusive scan, phase 1: each block scans 4096 counts in place (to offsets within the block)
@@ -1043,6 +1056,117 @@ __global__ void copy_back_kernel(CopyBackArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// two-level binning (tiles whose cells fit the shared-memory ordering, <= kMaxLocalCells)
+// level 1: counting sort by tile.  The particles arrive nearly in key order (binned before the
+//   last push, which moves them by about a cell), so the 32 lanes of a warp fall in one or two
+//   tiles: counts and cursors take one atomic per tile per warp (__match_any_sync), and the tile
+//   offsets come from a scan over the tiles only (no per-cell passes).
+// level 2: one CTA per tile orders the tile's particles by local cell (z fastest, then x, then y)
+//   with a shared-memory counting sort and writes them back into the species arrays.
+// ---------------------------------------------------------------------------
+constexpr int kMaxLocalCells = 4096;
+constexpr int kOrderThreads = 256;
+
+// per particle: key (sortedness check against its predecessor) and the tile histogram
+__global__ void tile_count_kernel(Key32Args a) {
+  if (gated_off(a.gate)) return;
+  bool mine = false;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int k = key_of(a, a.cell[p]);
+    const unsigned active = __activemask();
+    const int lane_id = threadIdx.x & 31;
+    const int up = __shfl_up_sync(active, k, 1);
+    const int prev = lane_id > 0 ? up : (p > 0 ? key_of(a, a.cell[p - 1]) : k);
+    mine |= prev > k;
+    const int t = k >> a.cpt_shift;
+    const unsigned peers = __match_any_sync(active, t);
+    if (lane_id == __ffs(peers) - 1) atomicAdd(a.counts + t, (uint32_t)__popc(peers));
+  }
+  flag_unsorted(a, mine);
+}
+
+struct TileScatterArgs {
+  const int* gate;
+  Key32Args k;
+  uint32_t* spc[8];                // the species arrays: cell, fx, fy, fz, ux, uy, uz, w as 32-bit words
+  uint32_t* tmp[8];                // scratch of the same layout
+  unsigned long long* id_spc;      // optional ids
+  unsigned long long* id_tmp;
+  const uint32_t* off;             // exclusive tile offsets
+  uint32_t* cursor;                // zeroed, per tile
+};
+
+// level 1: species arrays -> scratch, grouped by tile (order inside a tile: arbitrary)
+__global__ void tile_scatter_kernel(TileScatterArgs a) {
+  if (gated_off(a.gate)) return;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.k.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int t = key_of(a.k, (int)a.spc[0][p]) >> a.k.cpt_shift;
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, t);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(a.cursor + t, (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int64_t q = (int64_t)a.off[t] + base + rank;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) a.tmp[f][q] = a.spc[f][p];
+    if (a.id_spc) a.id_tmp[q] = a.id_spc[p];
+  }
+}
+
+// level 2: scratch -> species arrays, each tile ordered by local cell: one CTA per tile (grid-stride
+// over the tiles), a shared-memory counting sort (the order among the particles of one cell is
+// that of the shared-memory atomics, i.e. unspecified)
+__global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(TileScatterArgs a, const int64_t* tile_off,
+                                                                   int64_t n_tiles) {
+  if (gated_off(a.gate)) return;
+  __shared__ uint32_t cnt[kMaxLocalCells];
+  __shared__ uint32_t part[kOrderThreads];
+  const int cpt = 1 << a.k.cpt_shift;
+  const int lmask = cpt - 1;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t b0 = tile_off[t], nt = tile_off[t + 1] - b0;
+    if (nt == 0) continue;  // uniform over the CTA
+    for (int i = threadIdx.x; i < cpt; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < nt; i += blockDim.x)
+      atomicAdd(&cnt[key_of(a.k, (int)a.tmp[0][b0 + i]) & lmask], 1u);
+    __syncthreads();
+    // exclusive scan of cnt[0..cpt): each thread a run of cpt / blockDim entries
+    const int per = (cpt + blockDim.x - 1) / blockDim.x;
+    const int i0 = min(cpt, (int)threadIdx.x * per), i1 = min(cpt, i0 + per);
+    uint32_t sum = 0;
+    for (int i = i0; i < i1; ++i) sum += cnt[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+      const uint32_t v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0u;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    uint32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0u;
+    for (int i = i0; i < i1; ++i) {
+      const uint32_t c = cnt[i];
+      cnt[i] = run;
+      run += c;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) {
+      const int64_t j = b0 + i;
+      const int l = key_of(a.k, (int)a.tmp[0][j]) & lmask;
+      const int64_t q = b0 + atomicAdd(&cnt[l], 1u);
+#pragma unroll
+      for (int f = 0; f < 8; ++f) a.spc[f][q] = a.tmp[f][j];
+      if (a.id_spc) a.id_spc[q] = a.id_tmp[j];
+    }
+    __syncthreads();  // cnt is reused by the next tile
+  }
+}
+
 }  // namespace
 
 #ifndef PIC_BIN_LIMIT
@@ -1067,6 +1191,18 @@ pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float*
   a.rho = rho;
   a.gather = 1;
   return launch_push32(ctx, a);
+}
+
+bool bin32_two_level(const pic_ctx* ctx) {
+  return int64_t(ctx->tile[0]) * ctx->tile[1] * ctx->tile[2] <= kMaxLocalCells;
+}
+
+int bin32_launches(const pic_ctx* ctx, int64_t n, bool chunks, bool copy_back) {
+  // fill, (count), three scan kernels, (five chunk-list kernels), then for n > 0 the scatter gate,
+  // the cursor fill and the scatter (and the in-tile ordering, or the copy back)
+  const int head = 1 + (n > 0 ? 1 : 0) + 3 + (chunks ? 5 : 0);
+  if (n == 0) return head;
+  return head + 3 + ((bin32_two_level(ctx) || copy_back) ? 1 : 0);
 }
 
 bool tiled_push_fits(const pic_ctx* ctx) {
@@ -1111,6 +1247,28 @@ pic_status particles_deposit_rho32(pic_ctx* ctx, const pic_species32* sp, float*
   return launch_push32(ctx, a);
 }
 
+// chunk list of the tiled push from the tile ranges: chunks per tile, their exclusive scan and the
+// chunk -> tile map (see particles_push32_tiled)
+static pic_status build_chunks(pic_ctx* ctx, const int64_t* tile_off, uint32_t* chunks_out, const int* gate) {
+  const int64_t nt = ctx->n_tiles;
+  const int64_t nblk_t = (nt + kScanBlock - 1) / kScanBlock;
+  const unsigned fill_blocks = 152 * 8;
+  uint32_t* cbsum = chunks_out + nt + 1;
+  uint32_t* ctotal = cbsum + nblk_t;
+  chunk_count_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(tile_off, nt, chunks_out, gate);
+  PIC_LAUNCH_CHECK(ctx);
+  scan_block_kernel<<<(unsigned)std::min<int64_t>(nblk_t, 152 * 2), 1024, 0, ctx->stream>>>(chunks_out, nt, cbsum,
+                                                                                          gate);
+  PIC_LAUNCH_CHECK(ctx);
+  scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(cbsum, nblk_t, ctotal, gate);
+  PIC_LAUNCH_CHECK(ctx);
+  chunk_add_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(chunks_out, nt, cbsum, ctotal, gate);
+  PIC_LAUNCH_CHECK(ctx);
+  chunk_map_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(chunks_out, nt, chunks_out + chunk_map_offset(ctx), gate);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
+
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate,
                            uint32_t* chunks_out, bool copy_back) {
   const int64_t n = sp->n;
@@ -1126,8 +1284,6 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   uint32_t* bsum = counts + ncell;
   uint32_t* total = bsum + nblk;
   const unsigned fill_blocks = 152 * 8;
-  fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(counts, ncell, 0u, gate);
-  PIC_LAUNCH_CHECK(ctx);
   Key32Args b;
   b.gate = gate;
   b.cell = sp->cell;
@@ -1155,6 +1311,59 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   // binning costs a few microseconds, not a full-size launch
   const int bs = 256;
   const unsigned nb = (unsigned)std::min<int64_t>((n + bs - 1) / bs, fill_blocks);
+  int64_t* tile_off = offsets_out ? offsets_out : ctx->bin_counts;
+  if ((int64_t(1) << b.cpt_shift) <= kMaxLocalCells) {
+    // two-level: counting sort by tile, then by cell inside each tile (see tile_count_kernel)
+    const int64_t nt = ctx->n_tiles;
+    const int64_t nblk_t = (nt + kScanBlock - 1) / kScanBlock;
+    uint32_t* tcnt = counts;           // per tile: counts -> exclusive offsets
+    uint32_t* tbsum = counts + nt;     // scan block sums
+    uint32_t* ttotal = tbsum + nblk_t;
+    fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(tcnt, nt, 0u, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    if (n > 0) {
+      tile_count_kernel<<<nb, bs, 0, ctx->stream>>>(b);
+      PIC_LAUNCH_CHECK(ctx);
+    }
+    scan_block_kernel<<<(unsigned)std::min<int64_t>(nblk_t, 152 * 2), 1024, 0, ctx->stream>>>(tcnt, nt, tbsum, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(tbsum, nblk_t, ttotal, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    scan_add_kernel<<<(unsigned)std::min<int64_t>((nt + 255) / 256, fill_blocks), 256, 0, ctx->stream>>>(
+        tcnt, nt, tbsum, 0, tile_off, nt, ttotal, gate);
+    PIC_LAUNCH_CHECK(ctx);
+    if (chunks_out) PIC_TRY(build_chunks(ctx, tile_off, chunks_out, gate));
+    if (n == 0) {
+      PIC_CUDA_TRY(ctx, cudaMemsetAsync(sgate, 0, sizeof(int), ctx->stream));
+      return PIC_OK;
+    }
+    scatter_gate_kernel<<<1, 1, 0, ctx->stream>>>(gate, unsorted, sgate);
+    PIC_LAUNCH_CHECK(ctx);
+    if (!ctx->cell_cursor) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->cell_cursor, ncell * sizeof(uint32_t)));
+    fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(ctx->cell_cursor, nt, 0u, sgate);
+    PIC_LAUNCH_CHECK(ctx);
+    TileScatterArgs s;
+    s.gate = sgate;
+    s.k = b;
+    void* fields[8] = {sp->cell, sp->fx, sp->fy, sp->fz, sp->ux, sp->uy, sp->uz, sp->w};
+    uint32_t* tmp = reinterpret_cast<uint32_t*>(ctx->bin_tmp);
+    for (int f = 0; f < 8; ++f) {
+      s.spc[f] = static_cast<uint32_t*>(fields[f]);
+      s.tmp[f] = tmp + (int64_t)f * ctx->bin_cap;
+    }
+    s.id_spc = reinterpret_cast<unsigned long long*>(sp->id);
+    s.id_tmp = reinterpret_cast<unsigned long long*>(ctx->bin_tmp + 4 * ctx->bin_cap);  // words 8n..10n
+    s.off = tcnt;
+    s.cursor = ctx->cell_cursor;
+    tile_scatter_kernel<<<nb, bs, 0, ctx->stream>>>(s);
+    PIC_LAUNCH_CHECK(ctx);
+    cell_order_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 8), kOrderThreads, 0, ctx->stream>>>(s, tile_off, nt);
+    PIC_LAUNCH_CHECK(ctx);
+    return PIC_OK;  // the species arrays hold the binned particles
+  }
+  // one level: counting sort by cell in tile-major order over the whole grid
+  fill_u32_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(counts, ncell, 0u, gate);
+  PIC_LAUNCH_CHECK(ctx);
   if (n > 0) {
     key32_kernel<<<nb, bs, 0, ctx->stream>>>(b);
     PIC_LAUNCH_CHECK(ctx);
@@ -1163,28 +1372,10 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   PIC_LAUNCH_CHECK(ctx);
   scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(bsum, nblk, total, gate);
   PIC_LAUNCH_CHECK(ctx);
-  int64_t* tile_off = offsets_out ? offsets_out : ctx->bin_counts;
   scan_add_kernel<<<(unsigned)std::min<int64_t>((ncell + 255) / 256, fill_blocks), 256, 0, ctx->stream>>>(
-      counts, ncell, bsum, b.cpt_shift,
-                                                                           tile_off, ctx->n_tiles, total, gate);
+      counts, ncell, bsum, b.cpt_shift, tile_off, ctx->n_tiles, total, gate);
   PIC_LAUNCH_CHECK(ctx);
-  if (chunks_out) {
-    const int64_t nt = ctx->n_tiles;
-    const int64_t nblk_t = (nt + kScanBlock - 1) / kScanBlock;
-    uint32_t* cbsum = chunks_out + nt + 1;
-    uint32_t* ctotal = cbsum + nblk_t;
-    chunk_count_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(tile_off, nt, chunks_out, gate);
-    PIC_LAUNCH_CHECK(ctx);
-    scan_block_kernel<<<(unsigned)std::min<int64_t>(nblk_t, 152 * 2), 1024, 0, ctx->stream>>>(chunks_out, nt, cbsum,
-                                                                                            gate);
-    PIC_LAUNCH_CHECK(ctx);
-    scan_sums_kernel<<<1, 1024, 0, ctx->stream>>>(cbsum, nblk_t, ctotal, gate);
-    PIC_LAUNCH_CHECK(ctx);
-    chunk_add_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(chunks_out, nt, cbsum, ctotal, gate);
-    PIC_LAUNCH_CHECK(ctx);
-    chunk_map_kernel<<<fill_blocks, 256, 0, ctx->stream>>>(chunks_out, nt, chunks_out + chunk_map_offset(ctx), gate);
-    PIC_LAUNCH_CHECK(ctx);
-  }
+  if (chunks_out) PIC_TRY(build_chunks(ctx, tile_off, chunks_out, gate));
   if (n == 0) {
     PIC_CUDA_TRY(ctx, cudaMemsetAsync(sgate, 0, sizeof(int), ctx->stream));
     return PIC_OK;

@@ -212,13 +212,11 @@ using CPtr6 = CP6<double2>;
 // fft.cu ---------------------------------------------------------------------
 pic_status fft_setup(pic_ctx* ctx);
 // Forward R2C of ncomp real arrays into spectral arrays (plain DFT, unnormalised). T = double | float.
-// with_x = false stops after the z and y passes (the fused spectral step does the x pass).
 template <class T>
-pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp, bool with_x = true);
-// Inverse C2R (unnormalised); spectral arrays are destroyed.  with_x = false: the input has had its
-// x pass already (the fused spectral step), only the y and z passes run.
+pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, int ncomp);
+// Inverse C2R (unnormalised); spectral arrays are destroyed.
 template <class T>
-pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp, bool with_x = true);
+pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int ncomp);
 
 // psatd.cu -------------------------------------------------------------------
 long double fornberg_alpha_s(int m, int n);  // alpha^s_{m,n} (Eq. eq_Fornberg_staggered), host
@@ -238,14 +236,6 @@ pic_status psatd_phase(pic_ctx* ctx, CPtr6 in, CPtr6 out, const int* comp_kind, 
                        double scale);
 // G[c] = Z_c * src[c] * scale, src = the six E,B spectra given (paper convention) -> nodal DFT.
 pic_status psatd_to_nodal(pic_ctx* ctx, const double2* EB6, double scale);
-// Fused spectral step of the hybrid (and nodal) cycle: the x pass of the forward transforms of
-// J (3) and rho^{n+1} (J[c], rp hold them after the z and y passes), the update of every mode
-// (as psatd_update with g_mode 0, j_yee 0, the filter when the context has one), and the x pass of
-// the inverse transforms of the six G spectra, per column tile in shared memory.  On return: EB
-// updated, rp fully transformed (rho^{n+1} for the next step), J the Yee-centered spectrum if
-// write_j, G ready for the inverse y and z passes.  C = double2 | float2.
-template <class C>
-pic_status psatd_fused_step(pic_ctx* ctx, C* EB, C* J, const C* rn, C* rp, C* G, int write_j);
 // FP32-form counterparts (FP32 spectra, FP64 tables rounded at use).
 pic_status psatd_update32(pic_ctx* ctx, float2* EB, float2* J, const float2* rn, const float2* rp, float2* G,
                           int g_mode, int j_yee, int write_j, int smooth);
@@ -360,6 +350,12 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
 pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force);
 // device flag: the last particles_bin32 call permuted the species (its sorted copy is in bin_tmp)
 inline const int* bin32_scatter_gate(const pic_ctx* ctx) { return ctx->bin_flags + 1; }
+// tiles of at most 4096 cells are binned in two levels (by tile, then by cell inside each tile in
+// shared memory), which always leaves the sorted particles in the species arrays (copy_back is
+// implied); larger tiles by one counting sort over every cell
+bool bin32_two_level(const pic_ctx* ctx);
+// kernel launches of one particles_bin32 call (for the stage launch counters)
+int bin32_launches(const pic_ctx* ctx, int64_t n, bool chunks, bool copy_back);
 
 // center.cu -------------------------------------------------------------------
 pic_status center_to_nodal(pic_ctx* ctx, const double* const F[6], double* const out[6]);

@@ -17,7 +17,6 @@
 // of modest frequency, so the rule is exact to rounding).  a = 0 uses the
 // standard forms (Sec. 4.2) directly.
 #include "pic_internal.cuh"
-#include "fft_tile.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -301,10 +300,10 @@ struct UpdArgs {
 // (g_mode 1), times gscale.  The FP64 coefficient tables are read in FP64 and rounded to the data
 // precision at use.
 template <int VAR, class C>
-__device__ __forceinline__ void mode_update(const UpdArgs<C>& u, uint32_t ix, uint32_t iy, uint32_t iz, int64_t m,
-                                            C (&E)[3], C (&B)[3], C (&J)[3], C rn, C rp, C (&G)[6]) {
+__device__ __forceinline__ void mode_update(const UpdArgs<C>& u, uint32_t ix, uint32_t iy, uint32_t iz,
+                                            const C (&cf)[COEF_COUNT], C (&E)[3], C (&B)[3], C (&J)[3], C rn,
+                                            C rp, C (&G)[6]) {
   using T = decltype(C().x);
-  const int64_t qidx = u.coef.index(ix, iy, iz, u.nzh);
   const T k[3] = {(T)u.ks[0][ix], (T)u.ks[1][iy], (T)u.ks[2][iz]};
   const T zx = (T)u.zt[0][ix], zy = (T)u.zt[1][iy], zz = (T)u.zt[2][iz];
   if (!u.j_yee) {
@@ -330,9 +329,8 @@ __device__ __forceinline__ void mode_update(const UpdArgs<C>& u, uint32_t ix, ui
   cross(E, kE);
   cross(B, kB);
   cross(J, kJ);
-  auto co = [&](int idx) { return cast_c<C>(u.coef.get(idx, m, qidx)); };
-  const C TC = co(COEF_TC), TS = co(COEF_TS), X1 = co(COEF_X1), X2 = co(COEF_X2), TX3 = co(COEF_TX3),
-          X4 = co(COEF_X4);
+  const C TC = cf[COEF_TC], TS = cf[COEF_TS], X1 = cf[COEF_X1], X2 = cf[COEF_X2], TX3 = cf[COEF_TX3],
+          X4 = cf[COEF_X4];
   const T c2 = (T)u.c2;
   // rho term: i (theta^2 X3 rho^n - X2 rho^{n+1})
   const C rterm = cmuli(csub(cmul(TX3, rn), cmul(X2, rp)));
@@ -347,8 +345,8 @@ __device__ __forceinline__ void mode_update(const UpdArgs<C>& u, uint32_t ix, ui
   }
   C Ga[3], Gb[3];
   if (VAR == 2) {
-    const C P1 = co(COEF_PSI1), P2 = co(COEF_PSI2), Y1 = co(COEF_Y1), Y2 = co(COEF_Y2), Y3 = co(COEF_Y3),
-            Y4 = co(COEF_Y4);
+    const C P1 = cf[COEF_PSI1], P2 = cf[COEF_PSI2], Y1 = cf[COEF_Y1], Y2 = cf[COEF_Y2], Y3 = cf[COEF_Y3],
+            Y4 = cf[COEF_Y4];
     const C yr = cadd(cmul(Y3, rn), cmul(Y2, rp));
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -389,14 +387,11 @@ __device__ __forceinline__ void mode_update(const UpdArgs<C>& u, uint32_t ix, ui
   }
 }
 
-// One mode per thread over the whole spectrum.
+// load E, B, J, rho of mode m, update it with the coefficients cf, store E, B (J) and G
 template <int VAR, class C>
-__global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
-  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (m >= u.nmode) return;
+__device__ __forceinline__ void update_one(const UpdArgs<C>& u, int64_t m, uint32_t ix, uint32_t iy, uint32_t iz,
+                                           const C (&cf)[COEF_COUNT]) {
   const int64_t nm = u.nmode;
-  uint32_t ix, iy, iz;
-  mode_xyz(m, (uint32_t)u.nzh, __ffsll(u.Ny) - 1, ix, iy, iz);
   C E[3], B[3], J[3], G[6];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -404,7 +399,7 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
     B[a] = u.EB[(3 + a) * nm + m];
     J[a] = u.J[a * nm + m];
   }
-  mode_update<VAR>(u, ix, iy, iz, m, E, B, J, u.rn[m], u.rp[m], G);
+  mode_update<VAR>(u, ix, iy, iz, cf, E, B, J, u.rn[m], u.rp[m], G);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     u.EB[a * nm + m] = E[a];
@@ -418,97 +413,51 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
   for (int c = 0; c < 6; ++c) u.G[c * nm + m] = G[c];
 }
 
-// Fused spectral step: one CTA per (k_y, tile of W consecutive k_z columns), all Nx values of k_x.
-// Shared memory holds three pair buffers of [Nx][2W] complex values (element e of column w at
-// e * 2W + w): first the x-pass inputs J_x, J_y | J_z, rho^{n+1} (after their z and y passes),
-// transformed forward along x in place; then, mode by mode, the update reads J and rho^{n+1} from
-// them and writes the six G values over them (G_0, G_1 | G_2, G_3 | G_4, G_5; each mode's slots are
-// read before they are written, by the same thread), and the three buffers are transformed back
-// along x.  The CTA has Nx * W / 4 threads (8 elements of a pair buffer per thread in a pass).
-// Launch order pairs k_y and Ny - k_y (blockIdx.x = 2 q or 2 q + 1), so the two CTAs that read the
-// same compact-table entries run side by side.
-template <class C>
-struct FusedArgs {
-  UpdArgs<C> u;
-  const C* twx;  // x-axis twiddles exp(-2 pi i j / Nx)
-  int Nx, W;
-};
+// One mode per thread over the whole spectrum, coefficients from the full tables.
+template <int VAR, class C>
+__global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= u.nmode) return;
+  uint32_t ix, iy, iz;
+  mode_xyz(m, (uint32_t)u.nzh, __ffsll(u.Ny) - 1, ix, iy, iz);
+  C cf[COEF_COUNT];
+  constexpr int ncf = VAR == 2 ? COEF_COUNT : COEF_PSI1;
+#pragma unroll
+  for (int k = 0; k < ncf; ++k) cf[k] = cast_c<C>(__ldg(u.coef.full + k * u.nmode + m));
+  update_one<VAR>(u, m, ix, iy, iz, cf);
+}
 
-template <int VAR, class C, int MINB>
-__global__ void __launch_bounds__(256, MINB) fused_step_kernel(FusedArgs<C> f) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);
-  const UpdArgs<C>& u = f.u;
-  const int Nx = f.Nx, W = f.W, W2 = 2 * W;
-  const int lgW = pic_fft::lg2(W), lgNx = pic_fft::lg2(Nx);
-  const int Ny = (int)u.Ny, nzh = (int)u.nzh;
-  const int b = blockIdx.x;
-  const int ky = (b & 1) ? Ny - ((b + 1) >> 1) : (b >> 1);
-  const int col0 = blockIdx.y * W;
-  const int wv = min(W, nzh - col0);
-  const int64_t nm = u.nmode;
-  const int64_t xs = (int64_t)Ny * nzh;           // stride between k_x rows
-  const int64_t base = (int64_t)ky * nzh + col0;  // mode (0, ky, col0)
-  const int per = Nx * W;                         // elements of one set
-  C* const P0 = sm;
-  C* const P1 = sm + 2 * per;
-  C* const P2 = sm + 4 * per;
-  // 1. the x-pass inputs: set s -> buffer s / 2 (at sm + s / 2 * 2 per), columns (s % 2) W + w
-  for (int t = threadIdx.x; t < 4 * per; t += blockDim.x) {
-    const int s = t >> (lgNx + lgW), r = t & (per - 1);
-    const int e = r >> lgW, w = r & (W - 1);
-    const C* src = s < 3 ? u.J + s * nm : u.rp;
-    sm[(s >> 1) * 2 * per + e * W2 + (s & 1) * W + w] = w < wv ? src[base + e * xs + w] : czero<C>();
-  }
-  __syncthreads();
-  const pic_fft::LayCol lay{lgW + 1};
-  pic_fft::fft_tile<false>(P0, lay, Nx, f.twx, 1);
-  pic_fft::fft_tile<false>(P1, lay, Nx, f.twx, 1);
-  // 2. the update of every mode of the tile
-  for (int t = threadIdx.x; t < per; t += blockDim.x) {
-    const int e = t >> lgW, w = t & (W - 1);
-    const int i0 = e * W2 + w, i1 = i0 + W;
-    C G[6];
-    if (w < wv) {
-      const int64_t m = base + e * xs + w;
-      C E[3], B[3], J[3] = {P0[i0], P0[i1], P1[i0]};
-      const C rp = P1[i1];
+// One thread per entry (qx, qy, iz) of the compact tables: the coefficients are read once and
+// applied to the one, two or four modes (+-kx, +-ky, kz) that share them (qx = 0 and Nx / 2 have no
+// mirror along x, likewise along y).  REAL: the standard variant's real tables.
+template <int VAR, class C, bool REAL>
+__global__ void __launch_bounds__(256) update_quad_kernel(UpdArgs<C> u) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= u.coef.nq) return;
+  const uint32_t nzh = (uint32_t)u.nzh, nqy = (uint32_t)u.coef.nqy;
+  const uint32_t ee = (uint32_t)e;
+  const uint32_t r = ee / nzh, iz = ee - r * nzh;
+  const uint32_t qx = r / nqy, qy = r - qx * nqy;
+  C cf[COEF_COUNT];
+  constexpr int ncf = VAR == 2 ? COEF_COUNT : COEF_PSI1;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        E[a] = u.EB[a * nm + m];
-        B[a] = u.EB[(3 + a) * nm + m];
-      }
-      const_cast<C*>(u.rp)[m] = rp;  // rho^{n+1}, fully transformed: the next step's rho^n
-      mode_update<VAR>(u, (uint32_t)e, (uint32_t)ky, (uint32_t)(col0 + w), m, E, B, J, u.rn[m], rp, G);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        u.EB[a * nm + m] = E[a];
-        u.EB[(3 + a) * nm + m] = B[a];
-      }
-      if (u.write_j) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) u.J[a * nm + m] = J[a];
-      }
+  for (int k = 0; k < ncf; ++k) {
+    if (REAL) {
+      cf[k].x = (decltype(C().x))__ldg(u.coef.q + k * u.coef.nq + e);
+      cf[k].y = 0;
     } else {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) G[c] = czero<C>();
+      cf[k] = cast_c<C>(__ldg(reinterpret_cast<const double2*>(u.coef.q) + k * u.coef.nq + e));
     }
-    P0[i0] = G[0];
-    P0[i1] = G[1];
-    P1[i0] = G[2];
-    P1[i1] = G[3];
-    P2[i0] = G[4];
-    P2[i1] = G[5];
   }
-  __syncthreads();
-  // 3. the inverse x pass of the six G columns, then out
-  pic_fft::fft_tile<true>(P0, lay, Nx, f.twx, 1);
-  pic_fft::fft_tile<true>(P1, lay, Nx, f.twx, 1);
-  pic_fft::fft_tile<true>(P2, lay, Nx, f.twx, 1);
-  for (int t = threadIdx.x; t < 6 * per; t += blockDim.x) {
-    const int s = t >> (lgNx + lgW), r = t & (per - 1);
-    const int e = r >> lgW, w = r & (W - 1);
-    if (w < wv) u.G[s * nm + base + e * xs + w] = sm[(s >> 1) * 2 * per + e * W2 + (s & 1) * W + w];
+  const uint32_t Nx = (uint32_t)u.coef.nx, Ny = (uint32_t)u.coef.ny;
+  const int nmx = (qx == 0 || 2 * qx == Nx) ? 1 : 2, nmy = (qy == 0 || 2 * qy == Ny) ? 1 : 2;
+  for (int a = 0; a < nmx; ++a) {
+    const uint32_t ix = a ? Nx - qx : qx;
+    for (int b = 0; b < nmy; ++b) {
+      const uint32_t iy = b ? Ny - qy : qy;
+      const int64_t m = ((int64_t)ix * Ny + iy) * nzh + iz;
+      update_one<VAR>(u, m, ix, iy, iz, cf);
+    }
   }
 }
 
@@ -908,64 +857,20 @@ pic_status psatd_update_t(pic_ctx* ctx, C* EB, C* J, const C* rn, const C* rp, C
   u.j_yee = j_yee;
   u.write_j = write_j;
   const int bs = 256;
-  const unsigned nb = (unsigned)((ctx->nmode + bs - 1) / bs);
-  if (ctx->variant == PIC_PSATD_AVERAGED_GALILEAN)
-    update_kernel<2, C><<<nb, bs, 0, ctx->stream>>>(u);
-  else
-    update_kernel<0, C><<<nb, bs, 0, ctx->stream>>>(u);
-  PIC_LAUNCH_CHECK(ctx);
-  return PIC_OK;
-}
-
-static const double2* x_twiddles(const pic_ctx* ctx, double2*) { return ctx->twid[0]; }
-static const float2* x_twiddles(const pic_ctx* ctx, float2*) { return ctx->twid32[0]; }
-
-template <class C>
-pic_status psatd_fused_step(pic_ctx* ctx, C* EB, C* J, const C* rn, C* rp, C* G, int write_j) {
-  FusedArgs<C> f;
-  UpdArgs<C>& u = f.u;
-  u.EB = EB;
-  u.J = J;
-  u.rn = rn;
-  u.rp = rp;
-  u.coef = coef_view(ctx);
-  u.G = G;
-  for (int a = 0; a < 3; ++a) {
-    tab1d(ctx, a, &u.ks[a], &u.zt[a], &u.flt[a], &u.hs[a]);
-    if (ctx->filter_passes <= 0) u.flt[a] = nullptr;
-  }
-  u.Ny = ctx->N[1];
-  u.nzh = ctx->nzh;
-  u.nmode = ctx->nmode;
-  u.c2 = ctx->c * ctx->c;
-  u.gscale = 1.0 / (double)ctx->ncell;
-  u.g_mode = 0;
-  u.j_yee = 0;
-  u.write_j = write_j;
-  const int Nx = (int)ctx->N[0];
-  f.Nx = Nx;
-  f.W = std::min(16, 1024 / Nx);  // Nx * W <= 1024: at most 256 threads, 6 Nx W elements of shared memory
-  f.twx = x_twiddles(ctx, (C*)nullptr);
-  const int threads = Nx * f.W / 4;
-  const size_t smem = (size_t)6 * Nx * f.W * sizeof(C);
-  dim3 grid((unsigned)ctx->N[1], (unsigned)((ctx->nzh + f.W - 1) / f.W));
-  constexpr int minb = sizeof(C) == 8 ? 2 : 1;
   const bool avg = ctx->variant == PIC_PSATD_AVERAGED_GALILEAN;
-  if (avg) {
-    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fused_step_kernel<2, C, minb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-    fused_step_kernel<2, C, minb><<<grid, threads, smem, ctx->stream>>>(f);
+  if (ctx->coefq) {
+    const unsigned nb = (unsigned)((ctx->nq + bs - 1) / bs);
+    if (avg) update_quad_kernel<2, C, false><<<nb, bs, 0, ctx->stream>>>(u);
+    else if (ctx->coefq_real) update_quad_kernel<0, C, true><<<nb, bs, 0, ctx->stream>>>(u);
+    else update_quad_kernel<0, C, false><<<nb, bs, 0, ctx->stream>>>(u);
   } else {
-    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fused_step_kernel<0, C, minb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-    fused_step_kernel<0, C, minb><<<grid, threads, smem, ctx->stream>>>(f);
+    const unsigned nb = (unsigned)((ctx->nmode + bs - 1) / bs);
+    if (avg) update_kernel<2, C><<<nb, bs, 0, ctx->stream>>>(u);
+    else update_kernel<0, C><<<nb, bs, 0, ctx->stream>>>(u);
   }
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
-
-template pic_status psatd_fused_step<double2>(pic_ctx*, double2*, double2*, const double2*, double2*, double2*, int);
-template pic_status psatd_fused_step<float2>(pic_ctx*, float2*, float2*, const float2*, float2*, float2*, int);
 
 pic_status psatd_update_ex(pic_ctx* ctx, const double2* rn, const double2* rp, int g_mode, int j_yee,
                            int write_j, int smooth) {

@@ -135,7 +135,8 @@ void pic_destroy(pic_ctx* ctx) {
   void* ptrs[] = {ctx->k1d, ctx->twid[0], ctx->twid[1], ctx->twid[2], ctx->coef, ctx->EBh,
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
                   ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work, ctx->bin_gate,
-                  ctx->bin_outside, ctx->flt1d, ctx->bin_flags, ctx->k1d32, ctx->flt32, ctx->coefq};
+                  ctx->bin_outside, ctx->flt1d, ctx->bin_flags, ctx->k1d32, ctx->flt32, ctx->coefq,
+                  ctx->frame, ctx->dhist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) {

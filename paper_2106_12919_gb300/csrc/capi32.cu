@@ -210,6 +210,12 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
       PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_gate, sizeof(int)));
       PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_outside, sizeof(unsigned long long)));
       PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->bin_outside, 0, sizeof(unsigned long long), ctx->stream));
+      // drift-following tile frames: every species starts unshifted and at rest
+      PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->frame, 8 * PIC_MAX_BINNED_SPECIES * sizeof(int)));
+      PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->dhist, 10 * PIC_MAX_BINNED_SPECIES * sizeof(unsigned long long)));
+      PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->frame, 0, 8 * PIC_MAX_BINNED_SPECIES * sizeof(int), ctx->stream));
+      PIC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dhist, 0, 10 * PIC_MAX_BINNED_SPECIES * sizeof(unsigned long long),
+                                        ctx->stream));
     }
     for (int q = 0; q < n_species && q < PIC_MAX_BINNED_SPECIES; ++q) {
       if (!ctx->sp_off[q]) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->sp_off[q], (ctx->n_tiles + 1) * sizeof(int64_t)));
@@ -238,7 +244,7 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
     }
     if (st == PIC_OK) {
       StageScope t(ctx, STAGE_BIN, bin32_launches(ctx, sp[0].n, true, false));
-      st = particles_bin32(ctx, &sp[0], ctx->sp_off[0], ctx->bin_gate, ctx->sp_chunk[0], false);
+      st = particles_bin32(ctx, &sp[0], ctx->sp_off[0], ctx->bin_gate, ctx->sp_chunk[0], false, ctx->frame);
     }
     ctx->stream = main_stream;
     if (st != PIC_OK) return st;
@@ -301,15 +307,22 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
           PIC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));  // binned on the second stream
         } else {
           StageScope t(ctx, STAGE_BIN, bin32_launches(ctx, sp[q].n, true, false));
-          PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q], false));
+          PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q], false,
+                                    ctx->frame + 8 * q));
         }
         StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
         PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q], ctx->sp_chunk[q],
-                                         bin32_two_level(ctx) ? nullptr : bin32_scatter_gate(ctx)));
+                                         bin32_two_level(ctx) ? nullptr : bin32_scatter_gate(ctx),
+                                         ctx->frame + 8 * q, ctx->dhist + 10 * q));
       } else {
         StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
         PIC_TRY32(particles_push32(ctx, En, Bn, &sp[q], Jnp, rho));
       }
+    }
+    if (tiled) {
+      // the tile frames follow the species' drift (binning stays off while they keep their tiles)
+      StageScope t(ctx, STAGE_BIN, 1);
+      PIC_TRY32(particles_frames_advance(ctx, sp, n_species));
     }
     if (fd) {
       // J^{n+1/2}: optional smoothing, nodes -> Yee (work arrays: the nodal E, B, free after the

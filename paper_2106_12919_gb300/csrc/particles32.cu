@@ -40,6 +40,10 @@ struct Push32Args {
   const unsigned long long* id_src;
   unsigned long long* id_dst;
   float* w_dst;
+  // Tiled push only: the species' drift-following tile frame (shift [0..2], velocity [4..6]) and
+  // its displacement counters (see particles_frames_advance); null: no frame
+  const int* frame;
+  unsigned long long* dhist;
 };
 
 // shape of order P from the base cell i and the offset f in [0, 1)
@@ -164,9 +168,11 @@ __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window
   shape32<P>(ix, fx, lx, Sx);
   shape32<P>(iy, fy, ly, Sy);
   shape32<P>(iz, fz, lz, Sz);
-  const int wx = lx - win.org[0], wy = ly - win.org[1], wz = lz - win.org[2];
-  const bool inside = wx >= 0 && wy >= 0 && wz >= 0 && wx + NS <= win.W[0] && wy + NS <= win.W[1] &&
-                      wz + NS <= win.W[2];
+  // offsets from the window origin modulo N: the (shifted) tile frame may sit across the periodic
+  // boundary; a window longer than the grid along an axis holds the same node twice, and either
+  // entry flushes to it
+  const int wx = (lx - win.org[0]) & a.mask[0], wy = (ly - win.org[1]) & a.mask[1], wz = (lz - win.org[2]) & a.mask[2];
+  const bool inside = wx + NS <= win.W[0] && wy + NS <= win.W[1] && wz + NS <= win.W[2];
   if (!inside) {
     // rare (the particle left its tile since the last binning): global atomics, rolled loop
 #pragma unroll 1
@@ -451,10 +457,25 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   const int tile = s_tile;
   if (tile < 0) return;
   const int tz = tile % t.nt[2], ty = (tile / t.nt[2]) % t.nt[1], tx = tile / (t.nt[1] * t.nt[2]);
+  // the tile's cells start at tile * T + the species' frame shift (0 without a frame); the next push
+  // sees the frame moved by its velocity
+  __shared__ int s_next[3];  // first cell of the tile in the next push's frame, per axis
+  int fs[3] = {0, 0, 0};
+  if (a.frame) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fs[d] = __ldg(a.frame + d);
+  }
+  if (threadIdx.x < 3) {
+    const int d = threadIdx.x;
+    const int tc = d == 0 ? tx : (d == 1 ? ty : tz);
+    const int sh = d == 0 ? fs[0] : (d == 1 ? fs[1] : fs[2]);
+    const int te = d == 0 ? t.T[0] : (d == 1 ? t.T[1] : t.T[2]);
+    s_next[d] = tc * te + sh + (a.frame ? __ldg(a.frame + 4 + d) : 0);
+  }
   Window win;
-  win.org[0] = tx * t.T[0] - 2;
-  win.org[1] = ty * t.T[1] - 2;
-  win.org[2] = tz * t.T[2] - 2;
+  win.org[0] = tx * t.T[0] - 2 + fs[0];
+  win.org[1] = ty * t.T[1] - 2 + fs[1];
+  win.org[2] = tz * t.T[2] - 2 + fs[2];
   for (int d = 0; d < 3; ++d) win.W[d] = t.W[d];
   win.plane = t.wplane;
   win.comp = t.wcomp;
@@ -463,7 +484,7 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   // the staged fields are needed in phase 1 only and the deposit window in phase 2 only:
   // both live at the start of the dynamic shared memory
   float* fld = smem;  // [6][G0][G1][G2], plane stride gplane
-  const int go0 = tx * t.T[0] - 1, go1 = ty * t.T[1] - 1, go2 = tz * t.T[2] - 1;
+  const int go0 = tx * t.T[0] - 1 + fs[0], go1 = ty * t.T[1] - 1 + fs[1], go2 = tz * t.T[2] - 1 + fs[2];
   int p0, cnt;
   {
     const int64_t b0 = t.off[tile], cnt_t = t.off[tile + 1] - b0;
@@ -489,6 +510,9 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   // Phase 1: gather, Boris push and move of every particle of the chunk; the new state goes to
   // memory.  Each thread sums |q w v_c| (c = x, y, z) and |q w| over its particles.
   float bnd[4] = {0.f, 0.f, 0.f, 0.f};
+  // per thread: counts of the cell displacements -1 and +1 per axis in 5-bit fields (a thread
+  // visits at most ceil(2048 / 256) + 1 particles of its chunk)
+  unsigned dpk = 0u;
   const bool sorted_src = a.src_gate != nullptr && *a.src_gate != 0;
   for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
     const int pr = interleaved(j, q, s);
@@ -524,8 +548,8 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     shape32<P>(iy, fy, ly, Sy);
     shape32<P>(iz, fz, lz, Sz);
     float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const int gx = lx - go0, gy = ly - go1, gz = lz - go2;
-    const bool gin = gx >= 0 && gy >= 0 && gz >= 0 && gx + NS <= t.G[0] && gy + NS <= G1 && gz + NS <= G2;
+    const int gx = (lx - go0) & a.mask[0], gy = (ly - go1) & a.mask[1], gz = (lz - go2) & a.mask[2];
+    const bool gin = gx + NS <= t.G[0] && gy + NS <= G1 && gz + NS <= G2;
     if (gin) {
       // cubic: the outer loop stays rolled (a 4x smaller hot loop for the instruction cache,
       // measured 6% faster together with the deposit loop); lower orders fully unrolled
@@ -575,10 +599,13 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     // the next push gathers this particle from the staged nodes of this tile only while its new
     // cell stays in the tile: count those that leave (the device re-bins before the next push
     // when they exceed 2 % of all particles)
-    nout += ((unsigned)(nx - (go0 + 1)) >= (unsigned)t.T[0] || (unsigned)(ny - (go1 + 1)) >= (unsigned)t.T[1] ||
-             (unsigned)(nz - (go2 + 1)) >= (unsigned)t.T[2])
+    nout += (((nx - s_next[0]) & a.mask[0]) >= t.T[0] || ((ny - s_next[1]) & a.mask[1]) >= t.T[1] ||
+             ((nz - s_next[2]) & a.mask[2]) >= t.T[2])
                 ? 1u
                 : 0u;
+    // cell displacements -1 and +1 per axis (the frame velocity estimate of the next step)
+    dpk += (nx - ix == -1 ? 1u : 0u) + (nx - ix == 1 ? 1u << 5 : 0u) + (ny - iy == -1 ? 1u << 10 : 0u) +
+           (ny - iy == 1 ? 1u << 15 : 0u) + (nz - iz == -1 ? 1u << 20 : 0u) + (nz - iz == 1 ? 1u << 25 : 0u);
     a.cell[p] = (((nx & a.mask[0]) * (int)a.Ny + (ny & a.mask[1])) * (int)a.Nz) + (nz & a.mask[2]);
     a.fx[p] = nfx;
     a.fy[p] = nfy;
@@ -649,6 +676,13 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   }
   nout = __reduce_add_sync(0xffffffffu, nout);
   if (nout && (threadIdx.x & 31) == 0) atomicAdd(t.outside, (unsigned long long)nout);
+  if (a.dhist) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const unsigned c = __reduce_add_sync(0xffffffffu, (dpk >> (5 * e)) & 31u);
+      if (c && (threadIdx.x & 31) == 0) atomicAdd(a.dhist + e, (unsigned long long)c);
+    }
+  }
   __syncthreads();
   // flush the window: node (i, j, k) of the window is global node org + (i, j, k), wrapped
   float* dst[4] = {a.J[0], a.J[1], a.J[2], a.rho};
@@ -657,16 +691,17 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   for (int c = 0; c < 4; ++c) inv[c] = 1.0f / scale[c];
   const int W1 = t.W[1], W2 = t.W[2];
   if (t.vec_flush) {
-    // Window rows along z cover nodes [T0 - 2, T0 + T + 3); they are flushed as the aligned groups
-    // of 4 nodes starting at T0 - 4 (T0 and Nz are multiples of 4, so a group never wraps), one
-    // 16-byte vector reduction per group and component, nodes outside the window adding 0, groups
-    // whose four sums are all 0 skipped: about a third of the scalar reductions.
-    const int nq = (t.T[2] + 8) >> 2;
+    // Window rows along z cover nodes [org, org + W2); they are flushed as the aligned groups of 4
+    // nodes starting at org rounded down to a multiple of 4 (Nz is a multiple of 4, so a group
+    // never wraps), one 16-byte vector reduction per group and component, nodes outside the window
+    // adding 0, groups whose four sums are all 0 skipped: about a third of the scalar reductions.
+    const int z0 = win.org[2] & ~3;
+    const int nq = (win.org[2] - z0 + W2 + 3) >> 2;
     const int vol4 = t.W[0] * W1 * nq;
     for (int e = threadIdx.x; e < vol4; e += blockDim.x) {
       const int g = e % nq, r = e / nq;
       const int j = r % W1, i = r / W1;
-      const int k0 = 4 * g - 2;  // window index of the group's first node
+      const int k0 = z0 + 4 * g - win.org[2];  // window index of the group's first node
       const int o = (((win.org[0] + i) & a.mask[0]) * (int)a.Ny + ((win.org[1] + j) & a.mask[1])) * (int)a.Nz +
                     ((win.org[2] + k0) & a.mask[2]);
       const int d = i * t.wplane + j * W2 + k0;
@@ -733,6 +768,8 @@ Push32Args make_args32(pic_ctx* ctx, const pic_species32* sp) {
   a.id_src = nullptr;
   a.id_dst = nullptr;
   a.w_dst = nullptr;
+  a.frame = nullptr;
+  a.dhist = nullptr;
   return a;
 }
 
@@ -795,7 +832,7 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
   t.n_tiles = ctx->n_tiles;
   t.outside = ctx->bin_outside;
   const size_t smem = tile_layout(ctx, t);
-  bool aligned = ctx->tile[2] % 4 == 0 && ctx->N[2] % 4 == 0;
+  bool aligned = ctx->N[2] % 4 == 0;
   const float* dsts[4] = {a.J[0], a.J[1], a.J[2], a.rho};
   for (const float* d : dsts) aligned = aligned && (reinterpret_cast<uintptr_t>(d) % 16 == 0);
   t.vec_flush = aligned ? 1 : 0;
@@ -842,6 +879,32 @@ __global__ void bin_decide_kernel(int* gate, unsigned long long* outside, unsign
   *outside = 0ull;
 }
 
+struct FrameArgs {
+  int* frame;                 // + 8 q: shift [0..2], velocity [4..6]
+  unsigned long long* dhist;  // + 10 q: counts of displacements -1, +1 for x, y, z
+  int64_t n[PIC_MAX_BINNED_SPECIES];
+  int mask[3];
+  int nsp;
+};
+
+// one thread per species: the frame moves by the velocity the last push assumed; the new velocity
+// is the displacement at least 3/4 of the species' particles made (else 0)
+__global__ void frames_advance_kernel(FrameArgs a) {
+  const int q = threadIdx.x;
+  if (q >= a.nsp) return;
+  int* f = a.frame + 8 * q;
+  unsigned long long* h = a.dhist + 10 * q;
+  const unsigned long long n = (unsigned long long)a.n[q];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    f[d] = (f[d] + f[4 + d]) & a.mask[d];
+    const unsigned long long neg = h[2 * d], pos = h[2 * d + 1];
+    f[4 + d] = (n > 0 && 4 * neg >= 3 * n) ? -1 : ((n > 0 && 4 * pos >= 3 * n) ? 1 : 0);
+    h[2 * d] = 0ull;
+    h[2 * d + 1] = 0ull;
+  }
+}
+
 struct Key32Args {
   const int* gate;
   const int32_t* cell;
@@ -856,10 +919,22 @@ struct Key32Args {
   int32_t* key;
   uint32_t* counts;
   int* unsorted;           // set to 1 when some key is smaller than its predecessor's
+  const int* frame;        // the species' tile frame (shift at [0..2]) or null
+  int sh[3];               // its shift, loaded by each kernel (load_frame)
 };
 
+// the tile frame's shift into the kernel's copy of the arguments (0 without a frame)
+__device__ __forceinline__ Key32Args load_frame(const Key32Args& a) {
+  Key32Args k = a;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) k.sh[d] = a.frame ? __ldg(a.frame + d) : 0;
+  return k;
+}
+
+// key of a cell: tile of the cell shifted by -sh (the tile frame), then the local cell inside it
 __device__ __forceinline__ int key_of(const Key32Args& a, int c) {
-  const int cx = (c >> (a.shz + a.shy)) & a.mask[0], cy = (c >> a.shz) & a.mask[1], cz = c & a.mask[2];
+  const int cx = ((c >> (a.shz + a.shy)) - a.sh[0]) & a.mask[0], cy = ((c >> a.shz) - a.sh[1]) & a.mask[1],
+            cz = (c - a.sh[2]) & a.mask[2];
   const int t = (int)(((cx >> a.tshift[0]) * a.nty + (cy >> a.tshift[1])) * a.ntz + (cz >> a.tshift[2]));
   const int local = ((((cy & a.tmask[1]) << a.lshift_x) | (cx & a.tmask[0])) << a.lshift_z) | (cz & a.tmask[2]);
   return (t << a.cpt_shift) | local;
@@ -891,8 +966,9 @@ __device__ __forceinline__ void flag_unsorted(const Key32Args& a, bool mine) {
   if (threadIdx.x == 0 && s_any) *a.unsorted = 1;
 }
 
-__global__ void key32_kernel(Key32Args a) {
-  if (gated_off(a.gate)) return;
+__global__ void key32_kernel(Key32Args a0) {
+  if (gated_off(a0.gate)) return;
+  const Key32Args a = load_frame(a0);
   bool mine = false;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x)
     mine |= key32_one(a, p);
@@ -1069,8 +1145,9 @@ constexpr int kMaxLocalCells = 4096;
 constexpr int kOrderThreads = 256;
 
 // per particle: key (sortedness check against its predecessor) and the tile histogram
-__global__ void tile_count_kernel(Key32Args a) {
-  if (gated_off(a.gate)) return;
+__global__ void tile_count_kernel(Key32Args a0) {
+  if (gated_off(a0.gate)) return;
+  const Key32Args a = load_frame(a0);
   bool mine = false;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
     const int k = key_of(a, a.cell[p]);
@@ -1100,6 +1177,7 @@ struct TileScatterArgs {
 // level 1: species arrays -> scratch, grouped by tile (order inside a tile: arbitrary)
 __global__ void tile_scatter_kernel(TileScatterArgs a) {
   if (gated_off(a.gate)) return;
+  a.k = load_frame(a.k);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.k.n; p += (int64_t)gridDim.x * blockDim.x) {
     const int t = key_of(a.k, (int)a.spc[0][p]) >> a.k.cpt_shift;
     const unsigned active = __activemask();
@@ -1123,6 +1201,7 @@ __global__ void tile_scatter_kernel(TileScatterArgs a) {
 __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(TileScatterArgs a, const int64_t* tile_off,
                                                                    int64_t n_tiles) {
   if (gated_off(a.gate)) return;
+  a.k = load_frame(a.k);
   __shared__ uint32_t cnt[kMaxLocalCells];
   __shared__ uint32_t part[kOrderThreads];
   const int cpt = 1 << a.k.cpt_shift;
@@ -1180,6 +1259,19 @@ pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int for
   return PIC_OK;
 }
 
+pic_status particles_frames_advance(pic_ctx* ctx, const pic_species32* sp, int n_species) {
+  FrameArgs f;
+  f.frame = ctx->frame;
+  f.dhist = ctx->dhist;
+  f.nsp = std::min(n_species, PIC_MAX_BINNED_SPECIES);
+  for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) f.n[q] = q < f.nsp ? sp[q].n : 0;
+  for (int d = 0; d < 3; ++d) f.mask[d] = (int)ctx->N[d] - 1;
+  if (f.nsp <= 0 || !ctx->frame) return PIC_OK;
+  frames_advance_kernel<<<1, 32, 0, ctx->stream>>>(f);
+  PIC_LAUNCH_CHECK(ctx);
+  return PIC_OK;
+}
+
 pic_status particles_push32(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                             const pic_species32* sp, float* const J[3], float* rho) {
   Push32Args a = make_args32(ctx, sp);
@@ -1217,8 +1309,11 @@ size_t tile_chunk_words(const pic_ctx* ctx, int64_t n) {
 
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                                   const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets,
-                                  const uint32_t* chunks, const int* sorted_gate) {
+                                  const uint32_t* chunks, const int* sorted_gate, const int* frame,
+                                  unsigned long long* dhist) {
   Push32Args a = make_args32(ctx, sp);
+  a.frame = frame;
+  a.dhist = dhist;
   for (int c = 0; c < 3; ++c) {
     a.F[c] = En[c];
     a.F[3 + c] = Bn[c];
@@ -1270,7 +1365,7 @@ static pic_status build_chunks(pic_ctx* ctx, const int64_t* tile_off, uint32_t* 
 }
 
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate,
-                           uint32_t* chunks_out, bool copy_back) {
+                           uint32_t* chunks_out, bool copy_back, const int* frame) {
   const int64_t n = sp->n;
   pic_status st = particles_bin_capacity(ctx, n > 0 ? n : 1);
   if (st != PIC_OK) return st;
@@ -1302,6 +1397,8 @@ pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offse
   b.cpt_shift = ilog2(ctx->tile[0]) + ilog2(ctx->tile[1]) + ilog2(ctx->tile[2]);
   b.key = ctx->bin_tid;
   b.counts = counts;
+  b.frame = frame;
+  b.sh[0] = b.sh[1] = b.sh[2] = 0;
   if (!ctx->bin_flags) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->bin_flags, 2 * sizeof(int)));
   int* unsorted = ctx->bin_flags;
   int* sgate = ctx->bin_flags + 1;

@@ -148,6 +148,11 @@ struct pic_ctx {
   int64_t sp_off_n[PIC_MAX_BINNED_SPECIES];   // particle count they were built for, -1 = invalid
   uint32_t* sp_chunk[PIC_MAX_BINNED_SPECIES];  // per-species chunk lists of the tiled push (see below)
   int64_t sp_chunk_n[PIC_MAX_BINNED_SPECIES];  // particle count the chunk list was sized for
+  // FP32 form: drift-following tile frames, device ints per binned species q at frame + 8 q:
+  // [0..2] shift of the tile grid (cells, per axis), [4..6] frame velocity (cells per step);
+  // dhist + 10 q: the last push's per-axis counts of cell displacements -1, 0, +1 (and the total)
+  int* frame;
+  unsigned long long* dhist;
   Timers timers;
   char err[256];
 };
@@ -337,17 +342,24 @@ size_t tile_chunk_words(const pic_ctx* ctx, int64_t n);  // chunk list size for 
 pic_status particles_push32_tiled(pic_ctx* ctx, const float* const En[3], const float* const Bn[3],
                                   const pic_species32* sp, float* const J[3], float* rho, const int64_t* offsets,
                                   const uint32_t* chunks,
-                                  const int* sorted_gate = nullptr);
+                                  const int* sorted_gate = nullptr, const int* frame = nullptr,
+                                  unsigned long long* dhist = nullptr);
 // gate: device flag; the binning kernels do nothing while *gate == 0 (nullptr = always bin).
 // chunks_out (optional, tile_chunk_words entries): chunk starts for particles_push32_tiled.
 // copy_back = false leaves the sorted particles in ctx->bin_tmp (the species arrays untouched) for
 // a particles_push32_tiled call with sorted_gate = bin32_scatter_gate(ctx), which reads them there
 // when the binning permuted them and writes the pushed particles to the species arrays.  A species
 // already in key order gets its tile ranges only (no permutation): the scatter gate stays 0.
+// frame (optional): the species' drift-following tile frame (ctx->frame + 8 q); keys are taken from
+// the cell shifted by -frame[0..2].
 pic_status particles_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets_out, const int* gate = nullptr,
-                           uint32_t* chunks_out = nullptr, bool copy_back = true);
+                           uint32_t* chunks_out = nullptr, bool copy_back = true, const int* frame = nullptr);
 // *bin_gate = (particles whose new cell left their tile in the last tiled push > 2 % of total) || force
 pic_status particles_bin32_decide(pic_ctx* ctx, int64_t total_particles, int force);
+// After the pushes of a step: every binned species' tile frame moves by its frame velocity, and the
+// velocity becomes the cell displacement that at least 3/4 of the species' particles made in the
+// push just done (else 0); the displacement counts are cleared.
+pic_status particles_frames_advance(pic_ctx* ctx, const pic_species32* sp, int n_species);
 // device flag: the last particles_bin32 call permuted the species (its sorted copy is in bin_tmp)
 inline const int* bin32_scatter_gate(const pic_ctx* ctx) { return ctx->bin_flags + 1; }
 // tiles of at most 4096 cells are binned in two levels (by tile, then by cell inside each tile in

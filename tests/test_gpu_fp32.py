@@ -222,7 +222,30 @@ CASES = [
     ("laser_wakefield:half", dict(shape=(16, 16, 64), ppc=2), 100, False),
     ("thermal_plasma", dict(shape=(16, 16, 16), ppc=4), 100, True),
     ("galilean_drift", dict(shape=(16, 16, 32), ppc=1), 100, True),
+    # a thermal plasma streaming at 0.9 cells per step along +x and 0.4 along -y: the tiled push's
+    # tile frames follow the x drift (frame velocity +1) and stay put along y
+    ("drifting_plasma", dict(shape=(32, 16, 16), ppc=1), 40, True),
 ]
+
+
+def drifting_plasma(shape, ppc):
+    """An electron-positron plasma (no net current, so the drift is steady) streaming at
+    v = (0.9, -0.4, 0) c with thermal spread 0.01 c, standard PSATD, dx = dt = 1, quadratic shape."""
+    w = workloads.galilean_drift(shape=shape, ppc=ppc)
+    rng = np.random.default_rng(2024)
+    v = np.array([0.9, -0.4, 0.0])
+    g = 1.0 / np.sqrt(1.0 - v @ v)
+    sp = []
+    for s in w["species"]:
+        s = dict(s)
+        n = s["x"].size
+        s["ux"] = g * v[0] + rng.normal(0.0, 0.01, n)
+        s["uy"] = g * v[1] + rng.normal(0.0, 0.01, n)
+        s["uz"] = rng.normal(0.0, 0.01, n)
+        sp.append(s)
+    w["species"] = sp
+    w["params"] = dict(w["params"], variant=0, v_gal=(0.0, 0.0, 0.0), spectral_order=(0, 0, 0))
+    return w
 
 
 def _oracle_run(op, E, B, species, nsteps, noise=None):
@@ -261,7 +284,7 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
         opts = {"cycle": 1}
     if opt == "stag":
         opts = {"cycle": 2}
-    w = workloads.WORKLOADS[name](**kw)
+    w = drifting_plasma(**kw) if name == "drifting_plasma" else workloads.WORKLOADS[name](**kw)
     p = w["params"]
     shape, dx = p["shape"], p["dx"]
     if opt.startswith("fdtd"):

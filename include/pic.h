@@ -56,7 +56,7 @@ typedef enum {
   PIC_ERR_NOMEM = -3,        /* device allocation failed */
   PIC_ERR_CUDA = -4,         /* a CUDA call or kernel failed */
   PIC_ERR_CAPACITY = -5,     /* more particles than the context was sized for */
-  PIC_ERR_TIMEOUT = -6,      /* reserved: a bounded device-side wait gave up */
+  PIC_ERR_TIMEOUT = -6,      /* a bounded device-side wait (for a bulk copy) gave up; reported by pic_sync */
   PIC_ERR_NONFINITE = -7     /* reserved: non-finite values detected */
 } pic_status;
 
@@ -169,7 +169,9 @@ void pic_destroy(pic_ctx* ctx);
 /* Last error message of this context (static storage owned by the context). */
 const char* pic_last_error(const pic_ctx* ctx);
 
-/* Wait for the context's stream; returns PIC_ERR_CUDA if any enqueued work failed. */
+/* Wait for the context's stream; returns PIC_ERR_CUDA if any enqueued work failed, and
+ * PIC_ERR_TIMEOUT (once, the flag is cleared) if a kernel's bounded wait for one of its bulk
+ * copies gave up since the last pic_sync (the kernel then skipped its work: results are invalid). */
 pic_status pic_sync(pic_ctx* ctx);
 
 /*

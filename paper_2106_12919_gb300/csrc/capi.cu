@@ -136,7 +136,7 @@ void pic_destroy(pic_ctx* ctx) {
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
                   ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work, ctx->bin_gate,
                   ctx->bin_outside, ctx->flt1d, ctx->bin_flags, ctx->k1d32, ctx->flt32, ctx->coefq,
-                  ctx->frame, ctx->dhist};
+                  ctx->frame, ctx->dhist, ctx->dev_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) {
@@ -250,6 +250,8 @@ pic_status pic_init(pic_ctx** out, const int64_t grid[3], const double dx[3], do
          PIC_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
          PIC_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
          PIC_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+         PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->dev_err, sizeof(int)));
+         PIC_CUDA_TRY(ctx, cudaMemset(ctx->dev_err, 0, sizeof(int)));
          return PIC_OK;
        }()) != PIC_OK) {
     fprintf(stderr, "pic_init: %s\n", ctx->err);
@@ -269,6 +271,12 @@ pic_status pic_sync(pic_ctx* ctx) {
   if (!ctx) return PIC_ERR_ARG;
   PIC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   PIC_CUDA_TRY(ctx, cudaGetLastError());
+  int err = 0;
+  PIC_CUDA_TRY(ctx, cudaMemcpy(&err, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    PIC_CUDA_TRY(ctx, cudaMemset(ctx->dev_err, 0, sizeof(int)));
+    return pic_set_error(ctx, PIC_ERR_TIMEOUT, "a bounded wait for a bulk copy gave up; the results are invalid");
+  }
   return PIC_OK;
 }
 

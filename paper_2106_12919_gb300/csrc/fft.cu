@@ -29,16 +29,41 @@ using namespace pic_fft;
 template <class T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int Nz,
                                                                int64_t nlines, int L,
-                                                               const typename Cplx<T>::type* __restrict__ tw) {
+                                                               const typename Cplx<T>::type* __restrict__ tw,
+                                                               int bulk, int* err) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bar;
   C* sm = reinterpret_cast<C*>(smraw);
   const int M = Nz / 2;
-  const LayLine lay{M + (M >> kZPadShift)};
+  const LayLine lay{zline_len(M)};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
   const C* src = reinterpret_cast<const C*>(in.p[comp]);
-  {
+  if (bulk) {
+    // the CTA's lines are contiguous in global memory: one bulk copy per 16-element segment into
+    // its padded slot, issued by half of the threads, completing on one mbarrier
+    const int lgM = lg2(M);
+    const int lgS = lgM - kZPadShift;  // log2 segments per line
+    const int nvalid = (int)min((int64_t)L, nlines - line0);
+    const int nseg = nvalid << lgS;
+    constexpr uint32_t seg_bytes = 16 * sizeof(C);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, (uint32_t)nseg * seg_bytes);
+    for (int g = threadIdx.x; g < nseg; g += blockDim.x) {
+      const int l = g >> lgS, k = g & ((1 << lgS) - 1);
+      bulk_load(sm + lay.idx(k << kZPadShift, l), src + (line0 + l) * M + (k << kZPadShift), seg_bytes, &bar);
+    }
+    for (int t = (nvalid << lgM) + threadIdx.x; t < L * M; t += blockDim.x)  // lines past the end: zeros
+      sm[lay.idx(t & (M - 1), t >> lgM)] = czero<C>();
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      mbar_wait_bounded(&bar, 0);  // copies still in flight land before the CTA leaves
+      return;
+    }
+  } else {
     // L * M == 8 * blockDim.x: 8 elements per thread, loads issued back to back
     C v[8];
     const int lgM = lg2(M);
@@ -87,12 +112,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_r2c_kernel(
 template <class T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int Nz,
                                                                int64_t nlines, int L,
-                                                               const typename Cplx<T>::type* __restrict__ tw) {
+                                                               const typename Cplx<T>::type* __restrict__ tw,
+                                                               int bulk) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int M = Nz / 2;
-  const LayLine lay{M + (M >> kZPadShift)};
+  const LayLine lay{zline_len(M)};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
   const C* srcb = in.p[comp];
@@ -140,6 +166,19 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(
   fft_tile<true>(sm, lay, M, tw, 2);
   C* dst = reinterpret_cast<C*>(out.p[comp]);
   const int lgM = lg2(M);
+  if (bulk) {
+    // one bulk copy per 16-element segment from its padded slot to the contiguous lines
+    fence_proxy_async_shared();
+    __syncthreads();
+    const int lgS = lgM - kZPadShift;
+    const int nvalid = (int)min((int64_t)L, nlines - line0);
+    for (int g = threadIdx.x; g < (nvalid << lgS); g += blockDim.x) {
+      const int l = g >> lgS, k = g & ((1 << lgS) - 1);
+      bulk_store(dst + (line0 + l) * M + (k << kZPadShift), sm + lay.idx(k << kZPadShift, l), 16 * sizeof(C));
+    }
+    bulk_commit_and_wait_read();  // the shared memory is read before the CTA leaves
+    return;
+  }
   for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
     const int l = t >> lgM, e = t & (M - 1);
     const int64_t line = line0 + l;
@@ -220,10 +259,20 @@ pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp)
 
 int z_lines_per_cta(int Nz) { return kZTile / (Nz / 2); }
 
+// the z passes move lines by bulk copies when every real array starts 16-byte aligned and a line
+// holds whole 16-element segments
+template <class P>
+bool bulk_ok(const pic_ctx* ctx, P const* p, int ncomp) {
+  if (ctx->N[2] / 2 < 16 || !ctx->dev_err) return false;
+  for (int c = 0; c < ncomp; ++c)
+    if (reinterpret_cast<uintptr_t>(p[c]) % 16 != 0) return false;
+  return true;
+}
+
 template <class T>
 pic_status set_smem_attrs(pic_ctx* ctx) {
   using C = typename Cplx<T>::type;
-  const int zsm = (kZTile + (kZTile >> kZPadShift)) * (int)sizeof(C);
+  const int zsm = zline_len(kZTile) * (int)sizeof(C);
   PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
   PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
   const int ssm = 8192 * (int)sizeof(C);
@@ -286,8 +335,9 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
-  const size_t smem = (size_t)L * (Nz / 2 + ((Nz / 2) >> kZPadShift)) * sizeof(C);
-  fft_z_r2c_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2));
+  const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
+  fft_z_r2c_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2),
+                                                                      bulk_ok(ctx, in.p, ncomp) ? 1 : 0, ctx->dev_err);
   PIC_LAUNCH_CHECK(ctx);
   pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
   if (st != PIC_OK) return st;
@@ -305,8 +355,9 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
-  const size_t smem = (size_t)L * (Nz / 2 + ((Nz / 2) >> kZPadShift)) * sizeof(C);
-  fft_z_c2r_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2));
+  const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
+  fft_z_c2r_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2),
+                                                                      bulk_ok(ctx, out.p, ncomp) ? 1 : 0);
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }

@@ -7,14 +7,16 @@
 
 namespace pic_fft {
 
-constexpr int kZPadShift = 4;  // z-pass lines padded one slot per 16 elements (measured best of 4..32)
+// z-pass lines are padded 2 slots per 16 elements: the radix-8 scatter spreads over the banks, and
+// every 16-element segment starts 16-byte aligned, so it can move by one bulk copy
+constexpr int kZPadShift = 4;
 
 // All sizes are powers of two: index arithmetic uses shifts and masks (lg* = log2).
 __device__ __forceinline__ int lg2(int v) { return __ffs(v) - 1; }
 
-struct LayLine {  // z pass: element e of line l at l * LP + e + e / 16
+struct LayLine {  // z pass: element e of line l at l * LP + e + 2 (e / 16), LP = M + M / 8
   int LP;
-  __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + (e >> kZPadShift); }
+  __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + ((e >> kZPadShift) << 1); }
   // butterfly b of nb = 2^lgnb per line -> line l, index j
   __device__ __forceinline__ void map(int b, int lgnb, int& l, int& j) const {
     l = b >> lgnb;
@@ -141,6 +143,67 @@ __device__ void fft_tile(C* s, const LAY& lay, int N, const C* __restrict__ tw, 
   }
   if (rem == 2) stockham_pass<4, INV>(s, lay, lgN, lgNs, tw, twstride);
   else if (rem == 1) stockham_pass<2, INV>(s, lay, lgN, lgNs, tw, twstride);
+}
+
+// padded length of a z-pass line of M elements
+__host__ __device__ __forceinline__ int zline_len(int M) { return M + ((M >> kZPadShift) << 1); }
+
+// ---------------------------------------------------------------------------
+// bulk copies (the TMA engine's cp.async.bulk) between global and shared memory, completed on an
+// mbarrier; every wait is bounded and reports a timeout through a device flag
+// ---------------------------------------------------------------------------
+constexpr int kBulkWaitLimit = 1 << 22;  // try_wait polls before a wait gives up (far beyond any copy)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for phase `phase` of the barrier, at most kBulkWaitLimit polls; false when it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  for (int it = 0; it < kBulkWaitLimit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+// global -> shared, `bytes` (a multiple of 16, both addresses 16-byte aligned), completing on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// shared -> global, tracked by the issuing thread's bulk group
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_wait_read() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// make this thread's shared-memory writes visible to the bulk-copy (async) proxy
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 }  // namespace pic_fft

@@ -142,6 +142,7 @@ struct pic_ctx {
   int* bin_flags;                   // FP32 binning: [0] keys out of order, [1] scatter gate (see below)
   unsigned long long* bin_outside;  // FP32 form: particles whose new cell left their tile in the last push
 
+  int* dev_err;  // device flag: a bounded wait of a bulk copy gave up (PIC_ERR_TIMEOUT at pic_sync)
   int64_t steps_done;
   // FP32 form: per-species tile ranges of the last binning inside pic_step32
   int64_t* sp_off[PIC_MAX_BINNED_SPECIES];

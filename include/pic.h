@@ -24,7 +24,11 @@
  *   with no normalisation on the forward transform.
  * Pointers: every field and particle pointer is DEVICE memory owned by the
  *   caller, never freed or retained by the library; "host" pointers are named
- *   as such.  Work buffers, coefficient tables and the spectral field state
+ *   as such.  The transforms treat pairs of real elements as one complex value,
+ *   so the field arrays given to pic_step / pic_step32, pic_maxwell_step,
+ *   pic_adjoint_step and the pic_fft_* calls must start on a two-element
+ *   boundary (16 bytes for double, 8 for float; every cudaMalloc or torch
+ *   allocation does): PIC_ERR_ARG otherwise.  Work buffers, coefficient tables and the spectral field state
  *   belong to the context.
  * Streams: all work is enqueued on the context's stream (pic_ext.cuda_stream,
  *   default: the legacy default stream).  pic_step32 runs the first binning of a

@@ -264,6 +264,11 @@ extern "C" pic_status pic_adjoint_step(pic_ctx* ctx, const double* const E[3], c
                          "the adjoint covers the hybrid cycle with the Boris pusher and no smoothing");
   if (!nonnull(E, 3) || !nonnull(B, 3) || !nonnull(Ebar, 3) || !nonnull(Bbar, 3) || !rhobar)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
+  {
+    const void* ptrs[13] = {E[0], E[1], E[2], B[0], B[1], B[2], Ebar[0], Ebar[1], Ebar[2], Bbar[0], Bbar[1], Bbar[2],
+                            rhobar};
+    PIC_NEED_ALIGNED(ctx, ptrs, 13, 16);
+  }
   if (n_species < 0 || (n_species > 0 && (!sp || !spbar))) return pic_set_error(ctx, PIC_ERR_ARG, "species");
   for (int s = 0; s < n_species; ++s) {
     if (sp[s].n != spbar[s].n) return pic_set_error(ctx, PIC_ERR_ARG, "species %d: adjoint size mismatch", s);

@@ -338,6 +338,8 @@ pic_status pic_fft_forward(pic_ctx* ctx, const double* const real[], double* con
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (ncomp < 1 || ncomp > 6 || !all_nonnull(real, ncomp) || !all_nonnull(spec, ncomp))
     return pic_set_error(ctx, PIC_ERR_ARG, "fft arguments");
+  PIC_NEED_ALIGNED(ctx, real, ncomp, 16);
+  PIC_NEED_ALIGNED(ctx, spec, ncomp, 16);
   CRPtr6 in;
   CPtr6 o;
   for (int c = 0; c < ncomp; ++c) {
@@ -352,6 +354,8 @@ pic_status pic_fft_inverse(pic_ctx* ctx, double* const spec[], double* const rea
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (ncomp < 1 || ncomp > 6 || !all_nonnull(real, ncomp) || !all_nonnull(spec, ncomp))
     return pic_set_error(ctx, PIC_ERR_ARG, "fft arguments");
+  PIC_NEED_ALIGNED(ctx, real, ncomp, 16);
+  PIC_NEED_ALIGNED(ctx, spec, ncomp, 16);
   CPtr6 in;
   RPtr6 o;
   for (int c = 0; c < ncomp; ++c) {
@@ -368,6 +372,13 @@ pic_status pic_maxwell_step(pic_ctx* ctx, double* const E[3], double* const B[3]
   if (ctx->precision != PIC_FP64) return pic_set_error(ctx, PIC_ERR_ARG, "FP64 entry point on an FP32 context");
   if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || !all_nonnull(J, 3))
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
+  {
+    const void* ptrs[11] = {E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], rho_n, rho_np1};
+    PIC_NEED_ALIGNED(ctx, ptrs, 11, 16);
+    const void* avg[6] = {Eavg ? Eavg[0] : nullptr, Eavg ? Eavg[1] : nullptr, Eavg ? Eavg[2] : nullptr,
+                          Bavg ? Bavg[0] : nullptr, Bavg ? Bavg[1] : nullptr, Bavg ? Bavg[2] : nullptr};
+    PIC_NEED_ALIGNED(ctx, avg, 6, 16);
+  }
   if (ctx->cycle == PIC_CYCLE_HYBRID_FDTD) {
     const double* cJ[3] = {J[0], J[1], J[2]};
     return fdtd_update(ctx, E, B, cJ);
@@ -453,6 +464,11 @@ pic_status pic_step(pic_ctx* ctx, double* const E[3], double* const B[3], double
   if (!all_nonnull(E, 3) || !all_nonnull(B, 3) || (J && !all_nonnull(J, 3)) || !rho)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   if (nsteps < 0) return pic_set_error(ctx, PIC_ERR_ARG, "nsteps < 0");
+  {
+    const void* ptrs[10] = {E[0], E[1], E[2], B[0], B[1], B[2], J ? J[0] : nullptr, J ? J[1] : nullptr,
+                            J ? J[2] : nullptr, rho};
+    PIC_NEED_ALIGNED(ctx, ptrs, 10, 16);
+  }
   PIC_TRY(check_species(ctx, sp, n_species));
   if (nsteps == 0) return PIC_OK;
   if (ctx->cycle == PIC_CYCLE_HYBRID_FDTD) {

@@ -135,6 +135,8 @@ pic_status pic_fft_forward32(pic_ctx* ctx, const float* const real[], float* con
   PIC_NEED_FP32(ctx);
   if (ncomp < 1 || ncomp > 6 || !nonnull(real, ncomp) || !nonnull(spec, ncomp))
     return pic_set_error(ctx, PIC_ERR_ARG, "fft arguments");
+  PIC_NEED_ALIGNED(ctx, real, ncomp, 8);
+  PIC_NEED_ALIGNED(ctx, spec, ncomp, 8);
   CRP6<float> in;
   CP6<float2> o;
   for (int c = 0; c < ncomp; ++c) {
@@ -148,6 +150,8 @@ pic_status pic_fft_inverse32(pic_ctx* ctx, float* const spec[], float* const rea
   PIC_NEED_FP32(ctx);
   if (ncomp < 1 || ncomp > 6 || !nonnull(real, ncomp) || !nonnull(spec, ncomp))
     return pic_set_error(ctx, PIC_ERR_ARG, "fft arguments");
+  PIC_NEED_ALIGNED(ctx, real, ncomp, 8);
+  PIC_NEED_ALIGNED(ctx, spec, ncomp, 8);
   CP6<float2> in;
   RP6<float> o;
   for (int c = 0; c < ncomp; ++c) {
@@ -186,6 +190,11 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
   if (!nonnull(E, 3) || !nonnull(B, 3) || (J && !nonnull(J, 3)) || !rho)
     return pic_set_error(ctx, PIC_ERR_ARG, "null field pointer");
   if (nsteps < 0) return pic_set_error(ctx, PIC_ERR_ARG, "nsteps < 0");
+  {
+    const void* ptrs[10] = {E[0], E[1], E[2], B[0], B[1], B[2], J ? J[0] : nullptr, J ? J[1] : nullptr,
+                            J ? J[2] : nullptr, rho};
+    PIC_NEED_ALIGNED(ctx, ptrs, 10, 8);
+  }
   PIC_TRY32(check_species32(ctx, sp, n_species));
   if (nsteps == 0) return PIC_OK;
   const int64_t nm = ctx->nmode, nc = ctx->ncell;

@@ -485,12 +485,13 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   // both live at the start of the dynamic shared memory
   float* fld = smem;  // [6][G0][G1][G2], plane stride gplane
   const int go0 = tx * t.T[0] - 1 + fs[0], go1 = ty * t.T[1] - 1 + fs[1], go2 = tz * t.T[2] - 1 + fs[2];
-  int p0, cnt;
+  int p0, cnt, ppc;
   {
     const int64_t b0 = t.off[tile], cnt_t = t.off[tile + 1] - b0;
     const int64_t nch = t.chunk[tile + 1] - t.chunk[tile], k = s_part;
     p0 = (int)(b0 + cnt_t * k / nch);
     cnt = (int)(b0 + cnt_t * (k + 1) / nch) - p0;
+    ppc = (int)min((int64_t)cnt, (cnt_t + (t.cpt >> 1)) / t.cpt);  // particles per cell of the tile
   }
   const int gvol = t.G[0] * G1 * G2;
   for (int e = threadIdx.x; e < gvol; e += blockDim.x) {
@@ -503,8 +504,9 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   }
   __syncthreads();
   constexpr int NS = P + 1;
-  // visit every s-th particle (s ~ particles per cell) so that a warp's lanes hold distinct cells
-  const int s = max(1, min(8, (cnt + (t.cpt >> 1)) / t.cpt));
+  // visit every s-th particle (s ~ the tile's particles per cell) so that a warp's lanes hold
+  // distinct cells; a chunk of a dense tile spans only cnt / s cells, and its lanes spread over them
+  const int s = max(1, ppc);
   const int q = (cnt + s - 1) / s;
   unsigned nout = 0;
   // Phase 1: gather, Boris push and move of every particle of the chunk; the new state goes to

@@ -207,6 +207,21 @@ inline bool arrays_overlap(const void* const* in, int nin, const void* const* ou
   return false;
 }
 
+// The transforms read and write real arrays as pairs of elements (one complex value), so every real
+// array given to an entry point that transforms it must start on a two-element boundary (8 bytes in
+// the FP32 form, 16 in the FP64 form; every cudaMalloc or torch allocation does).  True when the
+// n non-null pointers are aligned to `bytes`.
+inline bool arrays_aligned(const void* const* p, int n, size_t bytes) {
+  for (int i = 0; i < n; ++i)
+    if (p[i] && reinterpret_cast<uintptr_t>(p[i]) % bytes != 0) return false;
+  return true;
+}
+#define PIC_NEED_ALIGNED(ctx, ptrs, n, bytes)                                                             \
+  do {                                                                                                   \
+    if (!arrays_aligned(reinterpret_cast<const void* const*>(ptrs), (n), (bytes)))                       \
+      return pic_set_error((ctx), PIC_ERR_ARG, "an array does not start on a %d-byte boundary", (int)(bytes)); \
+  } while (0)
+
 // Component pointer bundles passed by value to kernels.
 template <class T> struct RP6 { T* p[6]; };
 template <class T> struct CRP6 { const T* p[6]; };

@@ -357,7 +357,8 @@ def _errors(run, ref):
 @pytest.mark.parametrize("shape", [(16, 8, 64), (8, 8, 1024)])
 def test_fft32_unaligned_arrays_match_aligned(shape):
     """The z passes move lines by bulk copies when the real arrays start 16-byte aligned, and by
-    per-thread loads and stores otherwise: both give the same spectra and the same inverse."""
+    per-thread loads and stores when they start on the 8-byte (two-float) boundary only: both give
+    the same spectra and the same inverse.  An array off that boundary is refused (PIC_ERR_ARG)."""
     import torch
     p = dict(shape=shape, dx=(1.0, 1.0, 1.0), dt=0.5, shape_order=1, centering_order=(2, 2, 2), variant=0,
              v_gal=(0, 0, 0), spectral_order=(0, 0, 0), c=1.0, eps0=1.0)
@@ -366,19 +367,23 @@ def test_fft32_unaligned_arrays_match_aligned(shape):
     rng = np.random.default_rng(4)
     f = rng.normal(size=n).astype(np.float32)
     aligned = dev32(f)
-    buf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
-    buf[1:] = aligned
-    unaligned = buf[1:]                       # starts 4 bytes past a 256-byte boundary
-    assert unaligned.data_ptr() % 16 != 0 and aligned.data_ptr() % 16 == 0
+    buf = torch.zeros(n + 2, dtype=torch.float32, device="cuda")
+    buf[2:] = aligned
+    unaligned = buf[2:]                       # starts 8 bytes past a 256-byte boundary
+    assert unaligned.data_ptr() % 16 == 8 and aligned.data_ptr() % 16 == 0
+    # an array off the two-element boundary is refused before any device work
+    from paper_2106_12919_gb300 import pic
+    with pytest.raises(pic.PicError):
+        ctx.fft_forward32([buf[1:n + 1]], [torch.empty(2 * ctx.nmode, dtype=torch.float32, device="cuda")])
     specs = [torch.empty(2 * ctx.nmode, dtype=torch.float32, device="cuda") for _ in range(2)]
     ctx.fft_forward32([aligned], [specs[0]])
     ctx.fft_forward32([unaligned], [specs[1]])
     ctx.sync()
     np.testing.assert_array_equal(to_host(specs[0]), to_host(specs[1]))
-    obuf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    obuf = torch.zeros(n + 2, dtype=torch.float32, device="cuda")
     out_a = torch.empty(n, dtype=torch.float32, device="cuda")
     ctx.fft_inverse32([specs[0]], [out_a])
-    ctx.fft_inverse32([specs[1]], [obuf[1:]])
+    ctx.fft_inverse32([specs[1]], [obuf[2:]])
     ctx.sync()
-    np.testing.assert_array_equal(to_host(out_a), to_host(obuf[1:]))
+    np.testing.assert_array_equal(to_host(out_a), to_host(obuf[2:]))
     assert np.linalg.norm(to_host(out_a) / n - f) / np.linalg.norm(f) < 2e-6

@@ -55,6 +55,10 @@ SAMPLE_SHAPE = {"laser_wakefield": (32, 32, 128), "beam_wakefield": (32, 32, 128
                 "thermal_plasma": (16, 16, 32), "galilean_drift": (32, 32, 64), "seed_wave": (32, 32, 32)}
 FULL_SHAPE = {"laser_wakefield": (128, 128, 512), "beam_wakefield": (256, 256, 1024),
               "thermal_plasma": (32, 32, 32), "galilean_drift": (64, 64, 256), "seed_wave": (64, 64, 64)}
+# particle tile per workload (pic_ext.tile), from sweeps on one GB300 with the final kernels: at 1
+# particle per cell (beam-driven box) 8 x 16 x 8 beats 8 x 8 x 8 (push 8.70 against 8.94 ms per
+# step; 16 x 8 x 8 9.01, 16 x 16 x 8 9.84); at 2 per cell (laser-wakefield box) 8 x 8 x 8 is best
+TILE = {"beam_wakefield": (8, 16, 8)}
 # the other workloads, timed after the headline one: (name, forms)
 EXTRA_WORKLOADS = (("thermal_plasma", ("fp64", "fp32")), ("laser_wakefield", ("fp32", "fp64")),
                    ("galilean_drift", ("fp32", "fp64")))
@@ -335,11 +339,12 @@ def time_steps(ctx, step, E, B, J, rho, sp, steps, warmup, world, local):
     return max_over_ranks(ms, world), clocks, stage
 
 
-def e2e_roundtrip(ctx, fp32, E, B, rho, sp, steps, world, use_graph=True, copy_streams=1):
+def e2e_roundtrip(ctx, fp32, E, B, rho, sp, steps, world, use_graph=True, copy_streams=1, nbuf=3):
     """End to end through the public API with host buffers: every step copies its whole input
     state (E, B, rho and every particle array) from pinned host memory, runs pic_step(1) and copies
-    the whole advanced state (E, B, rho, particles) back into pinned host memory.  Two device copies
-    of the state alternate, so that the copies of step k +- 1 (own streams) overlap step k."""
+    the whole advanced state (E, B, rho, particles) back into pinned host memory.  nbuf device
+    copies of the state rotate, so that the input copy of the next step and the output copy of the
+    previous one (own streams) overlap a step."""
     import torch
     from paper_2106_12919_gb300 import pic
     stream = ctx.stream
@@ -347,24 +352,25 @@ def e2e_roundtrip(ctx, fp32, E, B, rho, sp, steps, world, use_graph=True, copy_s
     host_in = [t.cpu().pin_memory() for t in devs]
     host_out = [torch.empty(h.shape, dtype=h.dtype, pin_memory=True) for h in host_in]
     nbytes = sum(h.numel() * h.element_size() for h in host_in)
-    E2 = [torch.empty_like(t) for t in E]
-    B2 = [torch.empty_like(t) for t in B]
-    rho2 = torch.empty_like(rho)
-    sp2 = []
-    for s in sp:
-        arrs = [torch.empty_like(a) for a in s.arrays()]
-        sp2.append(pic.Species32(*arrs[:8], s.q, s.m) if fp32 else pic.Species(*arrs[:7], s.q, s.m))
-    sets = [(E, B, rho, sp), (E2, B2, rho2, sp2)]
-    bufs = [E + B + [rho] + [a for s in sp for a in s.arrays()],
-            E2 + B2 + [rho2] + [a for s in sp2 for a in s.arrays()]]
+    sets = [(E, B, rho, sp)]
+    for _ in range(nbuf - 1):
+        E2 = [torch.empty_like(t) for t in E]
+        B2 = [torch.empty_like(t) for t in B]
+        rho2 = torch.empty_like(rho)
+        sp2 = []
+        for s in sp:
+            arrs = [torch.empty_like(a) for a in s.arrays()]
+            sp2.append(pic.Species32(*arrs[:8], s.q, s.m) if fp32 else pic.Species(*arrs[:7], s.q, s.m))
+        sets.append((E2, B2, rho2, sp2))
+    bufs = [Eb + Bb + [rb] + [a for s in spb for a in s.arrays()] for Eb, Bb, rb, spb in sets]
     h2d_streams = [torch.cuda.Stream() for _ in range(copy_streams)]
     d2h_stream = torch.cuda.Stream()
-    copied = [[torch.cuda.Event() for _ in h2d_streams] for _ in range(2)]
-    done = [torch.cuda.Event(), torch.cuda.Event()]        # step on set b finished
-    read = [torch.cuda.Event(), torch.cuda.Event()]        # set b copied back to the host
+    copied = [[torch.cuda.Event() for _ in h2d_streams] for _ in range(nbuf)]
+    done = [torch.cuda.Event() for _ in range(nbuf)]        # step on set b finished
+    read = [torch.cuda.Event() for _ in range(nbuf)]        # set b copied back to the host
 
     def enqueue_h2d(k):
-        b = k % 2
+        b = k % nbuf
         for i, cs in enumerate(h2d_streams):
             with torch.cuda.stream(cs):
                 cs.wait_event(read[b])                     # set b's previous result has left the device
@@ -373,7 +379,7 @@ def e2e_roundtrip(ctx, fp32, E, B, rho, sp, steps, world, use_graph=True, copy_s
                 copied[b][i].record(cs)
 
     def enqueue_d2h(k):
-        b = k % 2
+        b = k % nbuf
         with torch.cuda.stream(d2h_stream):
             d2h_stream.wait_event(done[b])
             for d, h in zip(bufs[b], host_out):
@@ -384,7 +390,7 @@ def e2e_roundtrip(ctx, fp32, E, B, rho, sp, steps, world, use_graph=True, copy_s
     graphs = []
     if use_graph:
         capture = ctx.capture_step32 if fp32 else ctx.capture_step
-        for b in range(2):
+        for b in range(nbuf):
             for d, h in zip(bufs[b], host_in):
                 d.copy_(h)
             Eb, Bb, rb, spb = sets[b]
@@ -401,7 +407,7 @@ def e2e_roundtrip(ctx, fp32, E, B, rho, sp, steps, world, use_graph=True, copy_s
     for k in range(steps):
         if k + 1 < steps:
             enqueue_h2d(k + 1)
-        b = k % 2
+        b = k % nbuf
         Eb, Bb, rb, spb = sets[b]
         for ev in copied[b]:
             stream.wait_event(ev)
@@ -420,10 +426,10 @@ def e2e_roundtrip(ctx, fp32, E, B, rho, sp, steps, world, use_graph=True, copy_s
     out = {"value": job_throughput(npart, steps, world, ms), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "steps": steps,
            "note": "per step: pinned H2D of E, B, rho and every particle array, pic_step(1) (%s), D2H of the "
-                   "whole advanced state (E, B, rho, particles) into pinned host memory; two device copies of "
-                   "the state alternate so that the copies overlap the neighbouring steps" %
-                   ("replayed as a CUDA graph, pic.StepGraph" if graphs else "direct call")}
-    del graphs, sets, bufs, E2, B2, rho2, sp2, host_in, host_out
+                   "whole advanced state (E, B, rho, particles) into pinned host memory; %d device copies of "
+                   "the state rotate so that the copies overlap the neighbouring steps" %
+                   ("replayed as a CUDA graph, pic.StepGraph" if graphs else "direct call", nbuf)}
+    del graphs, sets, bufs, host_in, host_out
     return out
 
 
@@ -470,7 +476,8 @@ def run_form(form, w, args, world, rank, local, full=True):
     ncell = int(np.prod(p["shape"]))
     fp32 = form == "fp32"
     stream = torch.cuda.Stream()
-    ctx, E, B, J, rho, sp = setup_form(form, w, stream, args.tile)
+    tile = args.tile or TILE.get(w["name"].rsplit("_", 1)[0], (8, 8, 8))
+    ctx, E, B, J, rho, sp = setup_form(form, w, stream, tile)
     npart = sum(s.n for s in sp)
     step = ctx.step32 if fp32 else ctx.step
     (ctx.deposit_rho32 if fp32 else ctx.deposit_rho)(sp, rho)
@@ -485,7 +492,7 @@ def run_form(form, w, args, world, rank, local, full=True):
         out["roofline"] = push_roofline(w, fp32, stage, args.steps, npart, ncell, clocks, hbm)
         ke = args.e2e_steps or (max(3, min(args.steps, 10)) if fp32 else 3)
         out["e2e"] = e2e_roundtrip(ctx, fp32, E, B, rho, sp, ke, world, not args.e2e_no_graph,
-                                   args.e2e_copy_streams)
+                                   args.e2e_copy_streams, args.e2e_buffers)
         esz = 4 if fp32 else 8
         resident = (10 * ncell * esz + sum(sum(a.numel() * a.element_size() for a in s.arrays()) for s in sp)
                     + 40 * ncell * esz) / 1e9
@@ -556,12 +563,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--e2e-copy-streams", type=int, default=1,
                     help="streams the per-step host-to-device input copies are spread over")
+    ap.add_argument("--e2e-buffers", type=int, default=3,
+                    help="device copies of the state that rotate in the end-to-end loop")
     ap.add_argument("--e2e-no-graph", action="store_true",
                     help="end-to-end loop with direct pic_step calls instead of their CUDA graphs")
     ap.add_argument("--form", default="both", choices=["both", "fp32", "fp64"],
                     help="both: FP32 form timed as the headline, FP64 form beside it")
-    ap.add_argument("--tile", type=int, nargs=3, default=(8, 8, 8), metavar=("TX", "TY", "TZ"),
-                    help="particle tile edge in cells (pic_ext.tile)")
+    ap.add_argument("--tile", type=int, nargs=3, default=None, metavar=("TX", "TY", "TZ"),
+                    help="particle tile edge in cells (pic_ext.tile); default: the workload's (TILE)")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                     help="run the workload's generator on a smaller box (same dx, dt, physics), e.g. for profiling")
     args = ap.parse_args()
@@ -595,7 +604,7 @@ def main():
     config = workload_config(args.workload, world, shape)
     config["form"] = forms[0]
     config["particles"] = head["npart"]
-    config["tile"] = list(args.tile)
+    config["tile"] = list(args.tile or TILE.get(args.workload, (8, 8, 8)))
     config["cache"] = "working set (%.1f GB) > L2 (129 MB); no flush needed" % head["bytes_resident"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -416,7 +416,7 @@ pic_status pic_push_deposit32(pic_ctx* ctx, const float* const En[3], const floa
                               const pic_species32* sp, int n_species, float* const J_nodal[3], float* rho_nodal);
 
 /* pic_bin32: pic_bin in the FP32 form (tile from the integer cell index).  Inside a tile the
- * particles come out ordered by cell, x fastest, then z, then y (the order the tiled push's
+ * particles come out ordered by cell, z fastest, then x, then y (the order the tiled push's
  * shared-memory layout is built for); the order among particles of one cell is unspecified. */
 pic_status pic_bin32(pic_ctx* ctx, const pic_species32* sp, int64_t* offsets);
 

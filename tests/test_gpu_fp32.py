@@ -131,8 +131,8 @@ def test_bin32_offsets_exact():
     assert np.array_equal(np.sort(ids), np.arange(n))
     np.testing.assert_array_equal(to_host(d.cell), cell[ids])
     assert np.all(np.diff(tid[ids]) >= 0)
-    # inside a tile the particles are ordered by cell: x fastest, then z, then y
-    local = ((iy % tile[1]) * tile[2] + iz % tile[2]) * tile[0] + ix % tile[0]
+    # inside a tile the particles are ordered by cell: z fastest, then x, then y
+    local = ((iy % tile[1]) * tile[0] + ix % tile[0]) * tile[2] + iz % tile[2]
     key = tid * (tile[0] * tile[1] * tile[2]) + local
     assert np.all(np.diff(key[ids]) >= 0)
 

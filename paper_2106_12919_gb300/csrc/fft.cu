@@ -7,12 +7,14 @@
 // X_m = sum_j x_j exp(-2 pi i j.m / N) (App. A.1, Eq. Fourier_discrete without
 // the half-cell phase, which the caller applies).
 //
-// Every CTA loads a whole tile of lines into shared memory, runs the radix-8
-// (+ one radix-4 or radix-2) Stockham passes there, and writes the tile back.
-// z lines are contiguous (line-major tile, padded one slot per 16 elements to
-// spread the radix-8 scatter over the banks); y and x lines are strided, so a CTA
-// takes W adjacent columns (consecutive k_z) and the tile is element-major,
-// which keeps the global loads coalesced in W-element rows.
+// Every CTA transforms a whole tile of lines: radix-8 (+ one radix-4 or radix-2) Stockham passes
+// with every length a template parameter (one kernel per power of two, all index arithmetic
+// compile-time shifts and masks).  Pass 0 takes its butterfly's inputs straight from global memory
+// into registers, the last pass of a C2C or C2R transform writes straight back, so a transform of
+// npass passes goes through shared memory npass - 1 times.  z lines are contiguous (line-major
+// tile, padded 2 slots per 16 elements to spread the radix-8 scatter over the banks); y and x
+// lines are strided, so a CTA takes W adjacent columns (consecutive k_z) and the tile is
+// element-major, which keeps the global loads coalesced in W-element rows.
 #include "pic_internal.cuh"
 #include "fft_tile.cuh"
 
@@ -20,74 +22,39 @@
 
 namespace {
 
-constexpr int kZTile = 4096;    // complex elements per z-pass CTA (L lines * Nz/2)
-constexpr int kMaxThreads = 1024;
+constexpr int kZTile = 4096;  // complex elements per z-pass CTA (L lines * Nz/2): 512 threads
 
 using namespace pic_fft;
 
-// z-axis real-to-complex: L lines of Nz reals -> Nz/2+1 complex per line.
-template <class T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int Nz,
-                                                               int64_t nlines, int L,
-                                                               const typename Cplx<T>::type* __restrict__ tw,
-                                                               int bulk, int* err) {
+// z-axis real-to-complex: L = 4096 / M lines of Nz = 2M reals -> M + 1 complex per line.  Each
+// thread loads its pass-0 butterfly (8 packed (even, odd) pairs, stride M / 8) straight from global
+// memory.
+template <class T, int LGM>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
+    fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int64_t nlines,
+                     const typename Cplx<T>::type* __restrict__ tw) {
   using C = typename Cplx<T>::type;
+  constexpr int M = 1 << LGM, L = kZTile / M, lgnb = LGM - 3, nb = 1 << lgnb;
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ uint64_t bar;
   C* sm = reinterpret_cast<C*>(smraw);
-  const int M = Nz / 2;
   const LayLine lay{zline_len(M)};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
-  const C* src = reinterpret_cast<const C*>(in.p[comp]);
-  if (bulk) {
-    // the CTA's lines are contiguous in global memory: one bulk copy per 16-element segment into
-    // its padded slot, issued by half of the threads, completing on one mbarrier
-    const int lgM = lg2(M);
-    const int lgS = lgM - kZPadShift;  // log2 segments per line
-    const int nvalid = (int)min((int64_t)L, nlines - line0);
-    const int nseg = nvalid << lgS;
-    constexpr uint32_t seg_bytes = 16 * sizeof(C);
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, (uint32_t)nseg * seg_bytes);
-    for (int g = threadIdx.x; g < nseg; g += blockDim.x) {
-      const int l = g >> lgS, k = g & ((1 << lgS) - 1);
-      bulk_load(sm + lay.idx(k << kZPadShift, l), src + (line0 + l) * M + (k << kZPadShift), seg_bytes, &bar);
-    }
-    for (int t = (nvalid << lgM) + threadIdx.x; t < L * M; t += blockDim.x)  // lines past the end: zeros
-      sm[lay.idx(t & (M - 1), t >> lgM)] = czero<C>();
-    const bool ok = mbar_wait_bounded(&bar, 0);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicExch(err, 1);
-      mbar_wait_bounded(&bar, 0);  // copies still in flight land before the CTA leaves
-      return;
-    }
-  } else {
-    // L * M == 8 * blockDim.x: 8 elements per thread, loads issued back to back
+  {
+    const int l = threadIdx.x >> lgnb, j = threadIdx.x & (nb - 1);
+    const int64_t line = line0 + l;
+    const C* src = reinterpret_cast<const C*>(in.p[comp]) + line * M + j;
     C v[8];
-    const int lgM = lg2(M);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int t = threadIdx.x + q * blockDim.x;
-      const int l = t >> lgM;
-      const int64_t line = line0 + l;
-      v[q] = line < nlines ? src[line * M + (t & (M - 1))] : czero<C>();
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int t = threadIdx.x + q * blockDim.x;
-      sm[lay.idx(t & (M - 1), t >> lgM)] = v[q];
-    }
+    for (int r = 0; r < 8; ++r) v[r] = line < nlines ? src[r * nb] : czero<C>();
+    pass0_from_regs<false>(sm, lay, v, j, l);
   }
-  __syncthreads();
-  fft_tile<false>(sm, lay, M, tw, 2);
+  passes_ct<false, LGM, 1, Plan<LGM>::npass>(sm, lay, tw, 2);
   // split: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W^k (Z_k - conj Z_{M-k}),  W = exp(-2 pi i / Nz)
   C* dst = out.p[comp];
-  const int nzh = M + 1;
+  constexpr int nzh = M + 1, lgH = LGM - 1;
   const T h = (T)0.5;
   // k = 0 .. M/2 - 1 for every line (t < L M / 2), then k = M/2 (t >= L M / 2)
-  const int lgH = lg2(M) - 1;
   for (int t = threadIdx.x; t < (L << lgH) + L; t += blockDim.x) {
     const bool mid = t >= (L << lgH);
     const int l = mid ? t - (L << lgH) : t >> lgH;
@@ -109,28 +76,27 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_r2c_kernel(
 }
 
 // z-axis complex-to-real (unnormalised inverse); the imaginary parts of X_0, X_{Nz/2} are ignored.
-template <class T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int Nz,
-                                                               int64_t nlines, int L,
-                                                               const typename Cplx<T>::type* __restrict__ tw,
-                                                               int bulk) {
+// The last pass writes its outputs straight to global memory.
+template <class T, int LGM>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
+    fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int64_t nlines,
+                     const typename Cplx<T>::type* __restrict__ tw) {
   using C = typename Cplx<T>::type;
+  constexpr int M = 1 << LGM, L = kZTile / M;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int M = Nz / 2;
   const LayLine lay{zline_len(M)};
   const int comp = blockIdx.y;
   const int64_t line0 = (int64_t)blockIdx.x * L;
   const C* srcb = in.p[comp];
-  const int nzh = M + 1, P = M / 2 + 1;
+  constexpr int nzh = M + 1, P = M / 2 + 1, lgH = LGM - 1;
   // Z_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
   // k = 0 .. M/2 - 1 for every line (t < L M / 2), then k = M/2 (t >= L M / 2)
-  constexpr int kBatch = 5;  // L * P <= 5 * blockDim.x for every M >= 8 (L * M = 8 * blockDim.x)
-  const int lgH = lg2(M) - 1;
+  constexpr int kBatch = (L * P + 511) / 512;  // L * P <= 5 * 512 for every M >= 8
   C xk[kBatch], xm[kBatch];
 #pragma unroll
   for (int q = 0; q < kBatch; ++q) {
-    const int t = threadIdx.x + q * blockDim.x;
+    const int t = threadIdx.x + q * 512;
     const bool mid = t >= (L << lgH);
     const int l = mid ? t - (L << lgH) : t >> lgH;
     const int k = mid ? (M >> 1) : t & ((M >> 1) - 1);
@@ -143,7 +109,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(
   }
 #pragma unroll
   for (int q = 0; q < kBatch; ++q) {
-    const int t = threadIdx.x + q * blockDim.x;
+    const int t = threadIdx.x + q * 512;
     if (t >= L * P) break;
     const bool mid = t >= (L << lgH);
     const int l = mid ? t - (L << lgH) : t >> lgH;
@@ -163,65 +129,117 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2) fft_z_c2r_kernel(
     if (k != 0 && k != M - k) sm[lay.idx(M - k, l)] = cadd(cconj(A), cmuli(cmul(w, cconj(D))));
   }
   __syncthreads();
-  fft_tile<true>(sm, lay, M, tw, 2);
-  C* dst = reinterpret_cast<C*>(out.p[comp]);
-  const int lgM = lg2(M);
-  if (bulk) {
-    // one bulk copy per 16-element segment from its padded slot to the contiguous lines
-    fence_proxy_async_shared();
-    __syncthreads();
-    const int lgS = lgM - kZPadShift;
-    const int nvalid = (int)min((int64_t)L, nlines - line0);
-    for (int g = threadIdx.x; g < (nvalid << lgS); g += blockDim.x) {
-      const int l = g >> lgS, k = g & ((1 << lgS) - 1);
-      bulk_store(dst + (line0 + l) * M + (k << kZPadShift), sm + lay.idx(k << kZPadShift, l), 16 * sizeof(C));
-    }
-    bulk_commit_and_wait_read();  // the shared memory is read before the CTA leaves
-    return;
-  }
-  for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-    const int l = t >> lgM, e = t & (M - 1);
-    const int64_t line = line0 + l;
-    if (line < nlines) dst[line * M + e] = sm[lay.idx(e, l)];
-  }
+  passes_ct<true, LGM, 0, Plan<LGM>::npass - 1>(sm, lay, tw, 2);
+  C* dst = reinterpret_cast<C*>(out.p[comp]) + line0 * M;
+  const int nvalid = (int)min((int64_t)L, nlines - line0);
+  last_pass_to<true, LGM>(sm, lay, tw, 2, [&](int l, int e, C v) {
+    if (l < nvalid) dst[l * M + e] = v;
+  });
 }
 
-// In-place C2C along a strided axis: element e of column col of outer line o of
-// component c at p[c] + o * os + e * es + col.  A CTA takes W adjacent columns.
-// MAXT: the block size bound; the common 256-thread launches (N <= 128 with 16 columns) are
-// compiled for 5 resident CTAs per SM in FP32 (48 registers, no spills) and 4 in FP64, larger ones
-// for one.
-template <bool INV, class C, int MAXT>
-__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? (sizeof(C) == 8 ? 5 : 4) : 1) fft_strided_kernel(CP6<C> data, int N, int64_t es, int64_t os,
-                                                                 int ncols, int W, const C* __restrict__ tw) {
+// In-place C2C of length N = 2^LGN along a strided axis: element e of column col of outer line o
+// of component c at p[c] + o * os + e * es + col.  A CTA takes W = 2^LGW adjacent columns
+// (element-major tile, rows of W elements coalesced); pass 0 takes its inputs from global memory
+// and the last pass writes back to it.
+// resident CTAs per SM the register cap is set for: ~1280 threads (FP32, 48 registers) or 1024 (FP64, 64)
+template <int T, int C_BYTES>
+struct StridedMinBlocks {
+  static constexpr int raw = (C_BYTES == 16 ? 1024 : 1280) / T;
+  static constexpr int value = raw < 1 ? 1 : (raw > 16 ? 16 : raw);
+};
+
+template <bool INV, class C, int LGN, int LGW>
+__global__ void __launch_bounds__((1 << (LGN + LGW)) / 8, (StridedMinBlocks<(1 << (LGN + LGW)) / 8, sizeof(C)>::value))
+    fft_strided_kernel(CP6<C> data, int64_t es, int64_t os, int ncols, const C* __restrict__ tw) {
+  constexpr int N = 1 << LGN, W = 1 << LGW, nb = N / 8;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int lgW = lg2(W);
-  const LayCol lay{lgW};
+  const LayCol lay{LGW};
   const int comp = blockIdx.z;
   const int col0 = blockIdx.x * W;
   C* base = data.p[comp] + (int64_t)blockIdx.y * os + col0;
   const int wv = min(W, ncols - col0);
-  // N * W == 8 * blockDim.x: every thread moves 8 elements; the 8 loads are issued back to back
+  const int w = threadIdx.x & (W - 1), j = threadIdx.x >> LGW;
   C v[8];
+  {
+    const C* src = base + j * es + w;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int t = threadIdx.x + q * blockDim.x;
-    const int e = t >> lgW, w = t & (W - 1);
-    v[q] = w < wv ? base[e * es + w] : czero<C>();
+    for (int r = 0; r < 8; ++r) v[r] = w < wv ? src[r * nb * es] : czero<C>();
   }
+  if constexpr (LGN == 3) {  // one radix-8 pass: registers to global memory
+    dft<8, INV>(v);
+    if (w < wv) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) sm[threadIdx.x + q * blockDim.x] = v[q];
-  __syncthreads();
-  fft_tile<INV>(sm, lay, N, tw, 1);
-  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
-    const int e = t >> lgW, w = t & (W - 1);
-    if (w < wv) base[e * es + w] = sm[t];
+      for (int r = 0; r < 8; ++r) base[r * es + w] = v[r];
+    }
+  } else {
+    pass0_from_regs<INV>(sm, lay, v, j, w);
+    passes_ct<INV, LGN, 1, Plan<LGN>::npass - 1>(sm, lay, tw, 1);
+    last_pass_to<INV, LGN>(sm, lay, tw, 1, [&](int l, int e, C val) {
+      if (l < wv) base[e * es + l] = val;
+    });
   }
 }
 
-// columns per CTA of the strided passes (measured: 16 and 8 equal, 32 slower)
-int strided_width(int N) { return N >= 1024 ? 8 : 16; }
+// log2 of the columns per CTA of the strided passes (measured: 16 and 8 equal, 32 slower)
+constexpr int strided_lgw(int lgN) { return lgN >= 10 ? 3 : 4; }
+
+template <class C>
+using StridedFn = void (*)(CP6<C>, int64_t, int64_t, int, const C*);
+
+template <bool INV, class C, int LGN>
+StridedFn<C> strided_at() {
+  return fft_strided_kernel<INV, C, LGN, strided_lgw(LGN)>;
+}
+
+// the kernel for N = 2^lgN (8 <= N <= 1024)
+template <bool INV, class C>
+StridedFn<C> strided_fn(int lgN) {
+  switch (lgN) {
+    case 3: return strided_at<INV, C, 3>();
+    case 4: return strided_at<INV, C, 4>();
+    case 5: return strided_at<INV, C, 5>();
+    case 6: return strided_at<INV, C, 6>();
+    case 7: return strided_at<INV, C, 7>();
+    case 8: return strided_at<INV, C, 8>();
+    case 9: return strided_at<INV, C, 9>();
+    case 10: return strided_at<INV, C, 10>();
+  }
+  return nullptr;
+}
+
+template <class T>
+using ZR2CFn = void (*)(CRP6<T>, CP6<typename Cplx<T>::type>, int64_t, const typename Cplx<T>::type*);
+template <class T>
+using ZC2RFn = void (*)(CP6<typename Cplx<T>::type>, RP6<T>, int64_t, const typename Cplx<T>::type*);
+
+// the z kernels for M = Nz / 2 = 2^lgM (8 <= M <= 512)
+template <class T>
+ZR2CFn<T> z_r2c_fn(int lgM) {
+  switch (lgM) {
+    case 3: return fft_z_r2c_kernel<T, 3>;
+    case 4: return fft_z_r2c_kernel<T, 4>;
+    case 5: return fft_z_r2c_kernel<T, 5>;
+    case 6: return fft_z_r2c_kernel<T, 6>;
+    case 7: return fft_z_r2c_kernel<T, 7>;
+    case 8: return fft_z_r2c_kernel<T, 8>;
+    case 9: return fft_z_r2c_kernel<T, 9>;
+  }
+  return nullptr;
+}
+template <class T>
+ZC2RFn<T> z_c2r_fn(int lgM) {
+  switch (lgM) {
+    case 3: return fft_z_c2r_kernel<T, 3>;
+    case 4: return fft_z_c2r_kernel<T, 4>;
+    case 5: return fft_z_c2r_kernel<T, 5>;
+    case 6: return fft_z_c2r_kernel<T, 6>;
+    case 7: return fft_z_c2r_kernel<T, 7>;
+    case 8: return fft_z_c2r_kernel<T, 8>;
+    case 9: return fft_z_c2r_kernel<T, 9>;
+  }
+  return nullptr;
+}
 
 template <class C> const C* twiddles(const pic_ctx* ctx, int a);
 template <> const double2* twiddles<double2>(const pic_ctx* ctx, int a) { return ctx->twid[a]; }
@@ -230,7 +248,8 @@ template <> const float2* twiddles<float2>(const pic_ctx* ctx, int a) { return c
 template <class C>
 pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp) {
   const int N = (int)ctx->N[axis];
-  const int W = strided_width(N);
+  const int lgN = __builtin_ctz((unsigned)N);
+  const int W = 1 << strided_lgw(lgN);
   const int nzh = (int)ctx->nzh;
   int64_t es, os, nouter;
   if (axis == 1) {  // y: outer = x
@@ -242,46 +261,30 @@ pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp)
     os = nzh;
     nouter = ctx->N[1];
   }
+  StridedFn<C> fn = inv ? strided_fn<true, C>(lgN) : strided_fn<false, C>(lgN);
+  if (!fn) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", N);
   dim3 grid((nzh + W - 1) / W, (unsigned)nouter, ncomp);
-  const int threads = W * N / 8;
-  const size_t smem = (size_t)W * N * sizeof(C);
-  const C* tw = twiddles<C>(ctx, axis);
-  if (threads <= 256) {
-    if (inv) fft_strided_kernel<true, C, 256><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
-    else fft_strided_kernel<false, C, 256><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
-  } else {
-    if (inv) fft_strided_kernel<true, C, kMaxThreads><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
-    else fft_strided_kernel<false, C, kMaxThreads><<<grid, threads, smem, ctx->stream>>>(d, N, es, os, nzh, W, tw);
-  }
+  const size_t smem = N > 8 ? (size_t)W * N * sizeof(C) : 0;
+  fn<<<grid, W * N / 8, smem, ctx->stream>>>(d, es, os, nzh, twiddles<C>(ctx, axis));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
 
 int z_lines_per_cta(int Nz) { return kZTile / (Nz / 2); }
 
-// the z passes move lines by bulk copies when every real array starts 16-byte aligned and a line
-// holds whole 16-element segments
-template <class P>
-bool bulk_ok(const pic_ctx* ctx, P const* p, int ncomp) {
-  if (ctx->N[2] / 2 < 16 || !ctx->dev_err) return false;
-  for (int c = 0; c < ncomp; ++c)
-    if (reinterpret_cast<uintptr_t>(p[c]) % 16 != 0) return false;
-  return true;
-}
-
 template <class T>
 pic_status set_smem_attrs(pic_ctx* ctx) {
   using C = typename Cplx<T>::type;
-  const int zsm = zline_len(kZTile) * (int)sizeof(C);
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_r2c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_z_c2r_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
-  const int ssm = 8192 * (int)sizeof(C);
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<false, C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<true, C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<false, C, kMaxThreads>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
-  PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fft_strided_kernel<true, C, kMaxThreads>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  for (int lgM = 3; lgM <= 9; ++lgM) {
+    const int zsm = (kZTile >> lgM) * zline_len(1 << lgM) * (int)sizeof(C);
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(z_r2c_fn<T>(lgM), cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(z_c2r_fn<T>(lgM), cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
+  }
+  for (int lgN = 4; lgN <= 10; ++lgN) {
+    const int ssm = (1 << (lgN + strided_lgw(lgN))) * (int)sizeof(C);
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(strided_fn<false, C>(lgN), cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(strided_fn<true, C>(lgN), cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
+  }
   return PIC_OK;
 }
 
@@ -334,10 +337,11 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
   const int Nz = (int)ctx->N[2];
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
+  ZR2CFn<T> fn = z_r2c_fn<T>(__builtin_ctz((unsigned)(Nz / 2)));
+  if (!fn) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", Nz);
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  fft_z_r2c_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2),
-                                                                      bulk_ok(ctx, in.p, ncomp) ? 1 : 0, ctx->dev_err);
+  fn<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
   if (st != PIC_OK) return st;
@@ -354,10 +358,11 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
   const int Nz = (int)ctx->N[2];
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
+  ZC2RFn<T> fn = z_c2r_fn<T>(__builtin_ctz((unsigned)(Nz / 2)));
+  if (!fn) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", Nz);
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  fft_z_c2r_kernel<T><<<grid, L * (Nz / 2) / 8, smem, ctx->stream>>>(in, out, Nz, nlines, L, twiddles<C>(ctx, 2),
-                                                                      bulk_ok(ctx, out.p, ncomp) ? 1 : 0);
+  fn<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }

@@ -145,6 +145,79 @@ __device__ void fft_tile(C* s, const LAY& lay, int N, const C* __restrict__ tw, 
   else if (rem == 1) stockham_pass<2, INV>(s, lay, lgN, lgNs, tw, twstride);
 }
 
+// ---------------------------------------------------------------------------
+// Transforms of a compile-time length N = 2^LGN: radix-8 passes p = 0, 1, ... (Ns = 8^p) and one
+// radix-4 or radix-2 pass for the remaining bits; npass = ceil(LGN / 3).  Every index is a
+// compile-time shift or mask, the first pass can take its inputs from registers (loaded straight
+// from global memory) and the last pass can hand its outputs to global memory, so a transform moves
+// through shared memory npass - 1 times.
+// ---------------------------------------------------------------------------
+template <int LGN>
+struct Plan {
+  static constexpr int npass = (LGN + 2) / 3;
+};
+// log2 of the radix of pass P
+template <int LGN, int P>
+struct PassLgR {
+  static constexpr int value = LGN - 3 * P < 3 ? LGN - 3 * P : 3;
+};
+
+// passes P .. PEND - 1, shared memory to shared memory
+template <bool INV, int LGN, int P, int PEND, class C, class LAY>
+__device__ __forceinline__ void passes_ct(C* s, const LAY& lay, const C* __restrict__ tw, int twstride) {
+  if constexpr (P < PEND) {
+    stockham_pass<1 << PassLgR<LGN, P>::value, INV>(s, lay, LGN, 3 * P, tw, twstride);
+    passes_ct<INV, LGN, P + 1, PEND>(s, lay, tw, twstride);
+  }
+}
+
+// pass 0 (radix 8, no twiddles) on this thread's butterfly (j, l): v[r] = element j + r N / 8 of
+// line l; the outputs 8 j + r go to shared memory
+template <bool INV, class C, class LAY>
+__device__ __forceinline__ void pass0_from_regs(C* s, const LAY& lay, C (&v)[8], int j, int l) {
+  dft<8, INV>(v);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) s[lay.idx(8 * j + r, l)] = v[r];
+  __syncthreads();
+}
+
+// the last pass (Ns = N / R), from shared memory; out(l, e, value) receives element e of line l
+template <bool INV, int LGN, class C, class LAY, class OUT>
+__device__ __forceinline__ void last_pass_to(const C* s, const LAY& lay, const C* __restrict__ tw, int twstride,
+                                             OUT&& out) {
+  constexpr int P = Plan<LGN>::npass - 1;
+  constexpr int LGR = PassLgR<LGN, P>::value;
+  constexpr int R = 1 << LGR, PER = 8 / R;
+  constexpr int lgnb = LGN - LGR, nb = 1 << lgnb;  // nb = Ns
+  C v[PER][R];
+  int ol[PER], oj[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * blockDim.x;
+    int l, j;
+    lay.map(b, lgnb, l, j);
+    ol[q] = l;
+    oj[q] = j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q][r] = s[lay.idx(j + r * nb, l)];
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int k = oj[q];  // j < Ns: the butterfly's twiddle index and its first output
+    if (P > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = __ldg(&tw[k * r * twstride]);
+        if (INV) w.y = -w.y;
+        v[q][r] = cmul(v[q][r], w);
+      }
+    }
+    dft<R, INV>(v[q]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(ol[q], k + r * nb, v[q][r]);
+  }
+}
+
 // padded length of a z-pass line of M elements
 __host__ __device__ __forceinline__ int zline_len(int M) { return M + ((M >> kZPadShift) << 1); }
 

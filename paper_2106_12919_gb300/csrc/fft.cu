@@ -18,6 +18,7 @@
 #include "pic_internal.cuh"
 #include "fft_tile.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace {
@@ -137,6 +138,161 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
   });
 }
 
+// ---------------------------------------------------------------------------
+// Persistent FP32 z passes: a CTA walks over tiles t = blockIdx.x + i gridDim.x (every component's
+// tiles in turn) with a staging buffer in shared memory that one bulk copy (cp.async.bulk) fills
+// with the next tile's contiguous input while the CTA transforms the current one.  The copy
+// completes on an mbarrier whose waits are bounded: a wait that gives up sets the error flag (read
+// back by pic_sync as PIC_ERR_TIMEOUT), waits again (bounded) for the copy still in flight and
+// returns.
+// ---------------------------------------------------------------------------
+constexpr int kZPipeCtasPerSm = 3;
+
+struct ZPipe {
+  int64_t nlines;
+  int tiles_per_comp, ntiles;
+  int* err;
+};
+
+// issue the bulk copy of tile t's input (lines of `line_elems` elements of C) into the staging buffer
+template <class C, int L>
+__device__ __forceinline__ void zpipe_issue(const ZPipe& zp, const C* const* src, int line_elems, int t, C* stage,
+                                            uint64_t* bar) {
+  const int comp = t / zp.tiles_per_comp;
+  const int64_t line0 = (int64_t)(t - comp * zp.tiles_per_comp) * L;
+  const int nvalid = (int)min((int64_t)L, zp.nlines - line0);
+  const uint32_t bytes = (uint32_t)nvalid * line_elems * (uint32_t)sizeof(C);
+  fence_proxy_async_shared();  // the CTA's earlier reads of the buffer come before the copy's writes
+  mbar_arrive_expect_tx(bar, bytes);
+  bulk_load(stage, src[comp] + line0 * line_elems, bytes, bar);
+}
+
+// wait for the staging buffer's i-th fill; false (after recording the timeout) when it gave up
+__device__ __forceinline__ bool zpipe_wait(uint64_t* bar, int i, int* err) {
+  const bool ok = mbar_wait_bounded(bar, (uint32_t)(i & 1));
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    mbar_wait_bounded(bar, (uint32_t)(i & 1));  // the copy still in flight lands before the CTA leaves
+    return false;
+  }
+  return true;
+}
+
+template <int LGM>
+__global__ void __launch_bounds__(512, kZPipeCtasPerSm)
+    fft_z_r2c_pipe_kernel(CRP6<float> in, CP6<float2> out, ZPipe zp, const float2* __restrict__ tw) {
+  using C = float2;
+  constexpr int M = 1 << LGM, L = kZTile / M, lgnb = LGM - 3, nb = 1 << lgnb;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bar;
+  C* stage = reinterpret_cast<C*>(smraw);  // L lines x M, contiguous
+  C* sm = stage + L * M;                    // working tile, padded lines
+  const LayLine lay{zline_len(M)};
+  const C* const* src = reinterpret_cast<const C* const*>(in.p);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    if ((int)blockIdx.x < zp.ntiles) zpipe_issue<C, L>(zp, src, M, blockIdx.x, stage, &bar);
+  }
+  __syncthreads();
+  const int l0 = threadIdx.x >> lgnb, j0 = threadIdx.x & (nb - 1);
+  int i = 0;
+  for (int t = blockIdx.x; t < zp.ntiles; t += gridDim.x, ++i) {
+    const int comp = t / zp.tiles_per_comp;
+    const int64_t line0 = (int64_t)(t - comp * zp.tiles_per_comp) * L;
+    if (!zpipe_wait(&bar, i, zp.err)) return;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = stage[l0 * M + j0 + r * nb];  // lines past the end: never stored
+    __syncthreads();  // the staging buffer is free: fetch the next tile behind this one's passes
+    if (threadIdx.x == 0 && t + (int)gridDim.x < zp.ntiles) zpipe_issue<C, L>(zp, src, M, t + gridDim.x, stage, &bar);
+    pass0_from_regs<false>(sm, lay, v, j0, l0);
+    passes_ct<false, LGM, 1, Plan<LGM>::npass>(sm, lay, tw, 2);
+    // split: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W^k (Z_k - conj Z_{M-k}),  W = exp(-2 pi i / Nz)
+    C* dst = out.p[comp];
+    constexpr int nzh = M + 1, lgH = LGM - 1;
+    for (int u = threadIdx.x; u < (L << lgH) + L; u += blockDim.x) {
+      const bool mid = u >= (L << lgH);
+      const int l = mid ? u - (L << lgH) : u >> lgH;
+      const int k = mid ? (M >> 1) : u & ((M >> 1) - 1);
+      const int64_t line = line0 + l;
+      if (line >= zp.nlines) continue;
+      const C Zk = sm[lay.idx(k, l)];
+      const C Zm = sm[lay.idx((M - k) & (M - 1), l)];
+      C Fe, Fo;
+      Fe.x = 0.5f * (Zk.x + Zm.x);
+      Fe.y = 0.5f * (Zk.y - Zm.y);
+      Fo.x = 0.5f * (Zk.y + Zm.y);
+      Fo.y = -0.5f * (Zk.x - Zm.x);
+      const C wFo = cmul(__ldg(&tw[k]), Fo);
+      C* o = dst + line * nzh;
+      o[k] = cadd(Fe, wFo);
+      if (k != M - k) o[M - k] = cconj(csub(Fe, wFo));
+    }
+    __syncthreads();  // the working tile is read before the next tile's pass 0 writes it
+  }
+}
+
+template <int LGM>
+__global__ void __launch_bounds__(512, kZPipeCtasPerSm)
+    fft_z_c2r_pipe_kernel(CP6<float2> in, RP6<float> out, ZPipe zp, const float2* __restrict__ tw) {
+  using C = float2;
+  constexpr int M = 1 << LGM, L = kZTile / M, nzh = M + 1, P = M / 2 + 1, lgH = LGM - 1;
+  constexpr int kBatch = (L * P + 511) / 512;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bar;
+  C* stage = reinterpret_cast<C*>(smraw);            // L lines x (M + 1), contiguous
+  C* sm = stage + ((L * nzh + 1) & ~1);              // working tile, padded lines (16-byte aligned)
+  const LayLine lay{zline_len(M)};
+  const C* const* src = in.p;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    if ((int)blockIdx.x < zp.ntiles) zpipe_issue<C, L>(zp, src, nzh, blockIdx.x, stage, &bar);
+  }
+  __syncthreads();
+  int i = 0;
+  for (int t = blockIdx.x; t < zp.ntiles; t += gridDim.x, ++i) {
+    const int comp = t / zp.tiles_per_comp;
+    const int64_t line0 = (int64_t)(t - comp * zp.tiles_per_comp) * L;
+    const int nvalid = (int)min((int64_t)L, zp.nlines - line0);
+    if (!zpipe_wait(&bar, i, zp.err)) return;
+    // Z_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
+    // k = 0 .. M/2 - 1 for every line (u < L M / 2), then k = M/2 (u >= L M / 2)
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+      const int u = threadIdx.x + q * 512;
+      if (u >= L * P) break;
+      const bool mid = u >= (L << lgH);
+      const int l = mid ? u - (L << lgH) : u >> lgH;
+      const int k = mid ? (M >> 1) : u & ((M >> 1) - 1);
+      C Xk = czero<C>(), Xm = czero<C>();
+      if (l < nvalid) {
+        Xk = stage[l * nzh + k];
+        Xm = stage[l * nzh + M - k];
+      }
+      if (k == 0) {
+        Xk.y = 0;
+        Xm.y = 0;
+      }
+      C A, D;
+      A.x = Xk.x + Xm.x;
+      A.y = Xk.y - Xm.y;
+      D.x = Xk.x - Xm.x;
+      D.y = Xk.y + Xm.y;
+      const C w = __ldg(&tw[k]);
+      sm[lay.idx(k, l)] = cadd(A, cmuli(cmul(cconj(w), D)));
+      if (k != 0 && k != M - k) sm[lay.idx(M - k, l)] = cadd(cconj(A), cmuli(cmul(w, cconj(D))));
+    }
+    __syncthreads();  // the staging buffer is free: fetch the next tile behind this one's passes
+    if (threadIdx.x == 0 && t + (int)gridDim.x < zp.ntiles) zpipe_issue<C, L>(zp, src, nzh, t + gridDim.x, stage, &bar);
+    passes_ct<true, LGM, 0, Plan<LGM>::npass - 1>(sm, lay, tw, 2);
+    float2* dst = reinterpret_cast<float2*>(out.p[comp]) + line0 * M;
+    last_pass_to<true, LGM>(sm, lay, tw, 2, [&](int l, int e, C v) {
+      if (l < nvalid) dst[l * M + e] = v;
+    });
+    __syncthreads();  // the working tile is read before the next tile's pre-processing writes it
+  }
+}
+
 // In-place C2C of length N = 2^LGN along a strided axis: element e of column col of outer line o
 // of component c at p[c] + o * os + e * es + col.  A CTA takes W = 2^LGW adjacent columns
 // (element-major tile, rows of W elements coalesced); pass 0 takes its inputs from global memory
@@ -241,6 +397,52 @@ ZC2RFn<T> z_c2r_fn(int lgM) {
   return nullptr;
 }
 
+using ZR2CPipeFn = void (*)(CRP6<float>, CP6<float2>, ZPipe, const float2*);
+using ZC2RPipeFn = void (*)(CP6<float2>, RP6<float>, ZPipe, const float2*);
+
+ZR2CPipeFn z_r2c_pipe_fn(int lgM) {
+  switch (lgM) {
+    case 3: return fft_z_r2c_pipe_kernel<3>;
+    case 4: return fft_z_r2c_pipe_kernel<4>;
+    case 5: return fft_z_r2c_pipe_kernel<5>;
+    case 6: return fft_z_r2c_pipe_kernel<6>;
+    case 7: return fft_z_r2c_pipe_kernel<7>;
+    case 8: return fft_z_r2c_pipe_kernel<8>;
+    case 9: return fft_z_r2c_pipe_kernel<9>;
+  }
+  return nullptr;
+}
+ZC2RPipeFn z_c2r_pipe_fn(int lgM) {
+  switch (lgM) {
+    case 3: return fft_z_c2r_pipe_kernel<3>;
+    case 4: return fft_z_c2r_pipe_kernel<4>;
+    case 5: return fft_z_c2r_pipe_kernel<5>;
+    case 6: return fft_z_c2r_pipe_kernel<6>;
+    case 7: return fft_z_c2r_pipe_kernel<7>;
+    case 8: return fft_z_c2r_pipe_kernel<8>;
+    case 9: return fft_z_c2r_pipe_kernel<9>;
+  }
+  return nullptr;
+}
+
+// shared memory of the persistent z passes: staging buffer + working tile
+size_t z_pipe_smem(int lgM, bool c2r) {
+  const int M = 1 << lgM, L = kZTile / M;
+  const int stage = c2r ? ((L * (M + 1) + 1) & ~1) : L * M;
+  return (size_t)(stage + L * zline_len(M)) * sizeof(float2);
+}
+
+// the persistent z passes run when every array they copy in bulk starts 16-byte aligned (the
+// staging copies of a tile start at a multiple of 16 bytes from it, and move whole 16-byte units:
+// the line count is even)
+template <class P>
+bool z_pipe_ok(const pic_ctx* ctx, P const* p, int ncomp) {
+  if (!ctx->dev_err || ctx->nsm <= 0 || (ctx->N[0] * ctx->N[1]) % 2 != 0) return false;
+  for (int c = 0; c < ncomp; ++c)
+    if (reinterpret_cast<uintptr_t>(p[c]) % 16 != 0) return false;
+  return true;
+}
+
 template <class C> const C* twiddles(const pic_ctx* ctx, int a);
 template <> const double2* twiddles<double2>(const pic_ctx* ctx, int a) { return ctx->twid[a]; }
 template <> const float2* twiddles<float2>(const pic_ctx* ctx, int a) { return ctx->twid32[a]; }
@@ -280,6 +482,14 @@ pic_status set_smem_attrs(pic_ctx* ctx) {
     PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(z_r2c_fn<T>(lgM), cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
     PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(z_c2r_fn<T>(lgM), cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
   }
+  if (sizeof(T) == 4) {
+    for (int lgM = 3; lgM <= 9; ++lgM) {
+      PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(z_r2c_pipe_fn(lgM), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)z_pipe_smem(lgM, false)));
+      PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(z_c2r_pipe_fn(lgM), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)z_pipe_smem(lgM, true)));
+    }
+  }
   for (int lgN = 4; lgN <= 10; ++lgN) {
     const int ssm = (1 << (lgN + strided_lgw(lgN))) * (int)sizeof(C);
     PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(strided_fn<false, C>(lgN), cudaFuncAttributeMaxDynamicSharedMemorySize, ssm));
@@ -308,6 +518,11 @@ void sincospi_frac(int64_t p, int64_t q, double* s, double* c) {
 }
 
 pic_status fft_setup(pic_ctx* ctx) {
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      ctx->nsm = 0;
+  }
   for (int a = 0; a < 3; ++a) {
     const int64_t N = ctx->N[a];
     double2* h = new double2[N];
@@ -337,11 +552,24 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
   const int Nz = (int)ctx->N[2];
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
-  ZR2CFn<T> fn = z_r2c_fn<T>(__builtin_ctz((unsigned)(Nz / 2)));
-  if (!fn) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", Nz);
+  const int lgM = __builtin_ctz((unsigned)(Nz / 2));
+  if (lgM < 3 || lgM > 9) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", Nz);
+  if constexpr (sizeof(T) == 4) {
+    if (z_pipe_ok(ctx, in.p, ncomp)) {
+      const int tpc = (int)((nlines + L - 1) / L);
+      const ZPipe zp{nlines, tpc, tpc * ncomp, ctx->dev_err};
+      const int grid = std::min(zp.ntiles, kZPipeCtasPerSm * ctx->nsm);
+      z_r2c_pipe_fn(lgM)<<<grid, kZTile / 8, z_pipe_smem(lgM, false), ctx->stream>>>(in, out, zp,
+                                                                                     twiddles<C>(ctx, 2));
+      PIC_LAUNCH_CHECK(ctx);
+      pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
+      if (st != PIC_OK) return st;
+      return launch_strided<C>(ctx, out, 0, false, ncomp);
+    }
+  }
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  fn<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
+  z_r2c_fn<T>(lgM)<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
   if (st != PIC_OK) return st;
@@ -358,11 +586,22 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
   const int Nz = (int)ctx->N[2];
   const int L = z_lines_per_cta(Nz);
   const int64_t nlines = ctx->N[0] * ctx->N[1];
-  ZC2RFn<T> fn = z_c2r_fn<T>(__builtin_ctz((unsigned)(Nz / 2)));
-  if (!fn) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", Nz);
+  const int lgM = __builtin_ctz((unsigned)(Nz / 2));
+  if (lgM < 3 || lgM > 9) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", Nz);
+  if constexpr (sizeof(T) == 4) {
+    if (z_pipe_ok(ctx, in.p, ncomp)) {
+      const int tpc = (int)((nlines + L - 1) / L);
+      const ZPipe zp{nlines, tpc, tpc * ncomp, ctx->dev_err};
+      const int grid = std::min(zp.ntiles, kZPipeCtasPerSm * ctx->nsm);
+      z_c2r_pipe_fn(lgM)<<<grid, kZTile / 8, z_pipe_smem(lgM, true), ctx->stream>>>(in, out, zp,
+                                                                                    twiddles<C>(ctx, 2));
+      PIC_LAUNCH_CHECK(ctx);
+      return PIC_OK;
+    }
+  }
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  fn<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
+  z_c2r_fn<T>(lgM)<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }

@@ -88,6 +88,7 @@ struct pic_ctx {
   int filter_passes;  // bilinear smoothing passes of the deposits (0 = off)
   int pusher;         // pic_pusher
   int cycle;          // pic_cycle
+  int nsm;  // streaming multiprocessors of the device (persistent kernels size their grids by it)
   cudaStream_t stream;
   cudaStream_t aux;              // second stream (FP32 step: the first binning beside the entry transforms)
   cudaEvent_t ev_fork, ev_join;  // fork / join events between stream and aux

@@ -12,7 +12,7 @@
 // compile-time shifts and masks).  Pass 0 takes its butterfly's inputs straight from global memory
 // into registers, the last pass of a C2C or C2R transform writes straight back, so a transform of
 // npass passes goes through shared memory npass - 1 times.  z lines are contiguous (line-major
-// tile, padded 2 slots per 16 elements to spread the radix-8 scatter over the banks); y and x
+// tile, padded one slot per 16 elements to spread the radix-8 scatter over the banks); y and x
 // lines are strided, so a CTA takes W adjacent columns (consecutive k_z) and the tile is
 // element-major, which keeps the global loads coalesced in W-element rows.
 #include "pic_internal.cuh"
@@ -23,7 +23,8 @@
 
 namespace {
 
-constexpr int kZTile = 4096;  // complex elements per z-pass CTA (L lines * Nz/2): 512 threads
+constexpr int kZTile = 2048;             // complex elements per z-pass CTA (L lines * Nz/2)
+constexpr int kZThreads = kZTile / 8;    // one radix-8 butterfly per thread
 
 using namespace pic_fft;
 
@@ -31,7 +32,7 @@ using namespace pic_fft;
 // thread loads its pass-0 butterfly (8 packed (even, odd) pairs, stride M / 8) straight from global
 // memory.
 template <class T, int LGM>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kZThreads, (sizeof(T) == 4 ? 1536 : 1024) / kZThreads)
     fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int64_t nlines,
                      const typename Cplx<T>::type* __restrict__ tw) {
   using C = typename Cplx<T>::type;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
 // z-axis complex-to-real (unnormalised inverse); the imaginary parts of X_0, X_{Nz/2} are ignored.
 // The last pass writes its outputs straight to global memory.
 template <class T, int LGM>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kZThreads, (sizeof(T) == 4 ? 1536 : 1024) / kZThreads)
     fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int64_t nlines,
                      const typename Cplx<T>::type* __restrict__ tw) {
   using C = typename Cplx<T>::type;
@@ -93,11 +94,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
   constexpr int nzh = M + 1, P = M / 2 + 1, lgH = LGM - 1;
   // Z_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
   // k = 0 .. M/2 - 1 for every line (t < L M / 2), then k = M/2 (t >= L M / 2)
-  constexpr int kBatch = (L * P + 511) / 512;  // L * P <= 5 * 512 for every M >= 8
+  constexpr int kBatch = (L * P + kZThreads - 1) / kZThreads;
   C xk[kBatch], xm[kBatch];
 #pragma unroll
   for (int q = 0; q < kBatch; ++q) {
-    const int t = threadIdx.x + q * 512;
+    const int t = threadIdx.x + q * kZThreads;
     const bool mid = t >= (L << lgH);
     const int l = mid ? t - (L << lgH) : t >> lgH;
     const int k = mid ? (M >> 1) : t & ((M >> 1) - 1);
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
   }
 #pragma unroll
   for (int q = 0; q < kBatch; ++q) {
-    const int t = threadIdx.x + q * 512;
+    const int t = threadIdx.x + q * kZThreads;
     if (t >= L * P) break;
     const bool mid = t >= (L << lgH);
     const int l = mid ? t - (L << lgH) : t >> lgH;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 3 : 2)
 // back by pic_sync as PIC_ERR_TIMEOUT), waits again (bounded) for the copy still in flight and
 // returns.
 // ---------------------------------------------------------------------------
-constexpr int kZPipeCtasPerSm = 3;
+constexpr int kZPipeCtasPerSm = 1536 / kZThreads;
 
 struct ZPipe {
   int64_t nlines;
@@ -179,7 +180,7 @@ __device__ __forceinline__ bool zpipe_wait(uint64_t* bar, int i, int* err) {
 }
 
 template <int LGM>
-__global__ void __launch_bounds__(512, kZPipeCtasPerSm)
+__global__ void __launch_bounds__(kZThreads, kZPipeCtasPerSm)
     fft_z_r2c_pipe_kernel(CRP6<float> in, CP6<float2> out, ZPipe zp, const float2* __restrict__ tw) {
   using C = float2;
   constexpr int M = 1 << LGM, L = kZTile / M, lgnb = LGM - 3, nb = 1 << lgnb;
@@ -233,11 +234,11 @@ __global__ void __launch_bounds__(512, kZPipeCtasPerSm)
 }
 
 template <int LGM>
-__global__ void __launch_bounds__(512, kZPipeCtasPerSm)
+__global__ void __launch_bounds__(kZThreads, kZPipeCtasPerSm)
     fft_z_c2r_pipe_kernel(CP6<float2> in, RP6<float> out, ZPipe zp, const float2* __restrict__ tw) {
   using C = float2;
   constexpr int M = 1 << LGM, L = kZTile / M, nzh = M + 1, P = M / 2 + 1, lgH = LGM - 1;
-  constexpr int kBatch = (L * P + 511) / 512;
+  constexpr int kBatch = (L * P + kZThreads - 1) / kZThreads;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint64_t bar;
   C* stage = reinterpret_cast<C*>(smraw);            // L lines x (M + 1), contiguous
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(512, kZPipeCtasPerSm)
     // k = 0 .. M/2 - 1 for every line (u < L M / 2), then k = M/2 (u >= L M / 2)
 #pragma unroll
     for (int q = 0; q < kBatch; ++q) {
-      const int u = threadIdx.x + q * 512;
+      const int u = threadIdx.x + q * kZThreads;
       if (u >= L * P) break;
       const bool mid = u >= (L << lgH);
       const int l = mid ? u - (L << lgH) : u >> lgH;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(512, kZPipeCtasPerSm)
 // resident CTAs per SM the register cap is set for: ~1280 threads (FP32, 48 registers) or 1024 (FP64, 64)
 template <int T, int C_BYTES>
 struct StridedMinBlocks {
-  static constexpr int raw = (C_BYTES == 16 ? 1024 : 1280) / T;
+  static constexpr int raw = (C_BYTES == 16 ? 1024 : 1536) / T;
   static constexpr int value = raw < 1 ? 1 : (raw > 16 ? 16 : raw);
 };
 
@@ -559,7 +560,7 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
       const int tpc = (int)((nlines + L - 1) / L);
       const ZPipe zp{nlines, tpc, tpc * ncomp, ctx->dev_err};
       const int grid = std::min(zp.ntiles, kZPipeCtasPerSm * ctx->nsm);
-      z_r2c_pipe_fn(lgM)<<<grid, kZTile / 8, z_pipe_smem(lgM, false), ctx->stream>>>(in, out, zp,
+      z_r2c_pipe_fn(lgM)<<<grid, kZThreads, z_pipe_smem(lgM, false), ctx->stream>>>(in, out, zp,
                                                                                      twiddles<C>(ctx, 2));
       PIC_LAUNCH_CHECK(ctx);
       pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
@@ -569,7 +570,7 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
   }
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  z_r2c_fn<T>(lgM)<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
+  z_r2c_fn<T>(lgM)<<<grid, kZThreads, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
   if (st != PIC_OK) return st;
@@ -593,7 +594,7 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
       const int tpc = (int)((nlines + L - 1) / L);
       const ZPipe zp{nlines, tpc, tpc * ncomp, ctx->dev_err};
       const int grid = std::min(zp.ntiles, kZPipeCtasPerSm * ctx->nsm);
-      z_c2r_pipe_fn(lgM)<<<grid, kZTile / 8, z_pipe_smem(lgM, true), ctx->stream>>>(in, out, zp,
+      z_c2r_pipe_fn(lgM)<<<grid, kZThreads, z_pipe_smem(lgM, true), ctx->stream>>>(in, out, zp,
                                                                                     twiddles<C>(ctx, 2));
       PIC_LAUNCH_CHECK(ctx);
       return PIC_OK;
@@ -601,7 +602,7 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
   }
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  z_c2r_fn<T>(lgM)<<<grid, kZTile / 8, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
+  z_c2r_fn<T>(lgM)<<<grid, kZThreads, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }

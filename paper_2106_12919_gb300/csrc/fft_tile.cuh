@@ -7,16 +7,16 @@
 
 namespace pic_fft {
 
-// z-pass lines are padded 2 slots per 16 elements: the radix-8 scatter spreads over the banks, and
-// every 16-element segment starts 16-byte aligned, so it can move by one bulk copy
+// z-pass lines are padded one slot per 16 elements: the radix-8 scatter of pass 0 (outputs 8 j + r)
+// then spreads a warp's lanes over all banks
 constexpr int kZPadShift = 4;
 
 // All sizes are powers of two: index arithmetic uses shifts and masks (lg* = log2).
 __device__ __forceinline__ int lg2(int v) { return __ffs(v) - 1; }
 
-struct LayLine {  // z pass: element e of line l at l * LP + e + 2 (e / 16), LP = M + M / 8
+struct LayLine {  // z pass: element e of line l at l * LP + e + e / 16, LP = M + M / 16
   int LP;
-  __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + ((e >> kZPadShift) << 1); }
+  __device__ __forceinline__ int idx(int e, int l) const { return l * LP + e + (e >> kZPadShift); }
   // butterfly b of nb = 2^lgnb per line -> line l, index j
   __device__ __forceinline__ void map(int b, int lgnb, int& l, int& j) const {
     l = b >> lgnb;
@@ -219,7 +219,7 @@ __device__ __forceinline__ void last_pass_to(const C* s, const LAY& lay, const C
 }
 
 // padded length of a z-pass line of M elements
-__host__ __device__ __forceinline__ int zline_len(int M) { return M + ((M >> kZPadShift) << 1); }
+__host__ __device__ __forceinline__ int zline_len(int M) { return M + (M >> kZPadShift); }
 
 // ---------------------------------------------------------------------------
 // bulk copies (the TMA engine's cp.async.bulk) between global and shared memory, completed on an

@@ -136,7 +136,7 @@ void pic_destroy(pic_ctx* ctx) {
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
                   ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work, ctx->bin_gate,
                   ctx->bin_outside, ctx->flt1d, ctx->bin_flags, ctx->k1d32, ctx->flt32, ctx->coefq,
-                  ctx->frame, ctx->dhist, ctx->dev_err};
+                  ctx->coefq32, ctx->frame, ctx->dhist, ctx->dev_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < PIC_MAX_BINNED_SPECIES; ++q) {

@@ -114,6 +114,9 @@ struct pic_ctx {
   // quarter ix <= Nx/2, iy <= Ny/2 of the (kx, ky) plane holds them all ([ncoef][nqx][nqy][nzh]);
   // real doubles for the standard variant (every coefficient is real there), double2 otherwise.
   double* coefq;
+  // FP32 contexts: the same rounded to FP32 (float or float2), which the FP32 update reads; it
+  // rounds every FP64 coefficient to FP32 at use, so the values are the same at half the traffic
+  float* coefq32;
   int coefq_real;
   int64_t nqx, nqy, nq;
 
@@ -308,6 +311,7 @@ __device__ __forceinline__ void vay_push(T& ux, T& uy, T& uz, const T* f, T k, T
 // them, else the full [ncoef][nmode] tables.
 struct CoefView {
   const double* q;       // compact tables (NULL: use full)
+  const float* q32;      // their FP32 copy (FP32 contexts) or NULL
   const double2* full;   // full tables
   int real;              // compact tables hold real doubles
   int64_t nqy, nq, nmode;
@@ -326,6 +330,7 @@ struct CoefView {
 inline CoefView coef_view(const pic_ctx* ctx) {
   CoefView v;
   v.q = ctx->coefq;
+  v.q32 = ctx->coefq32;
   v.full = ctx->coef;
   v.real = ctx->coefq_real;
   v.nqy = ctx->nqy;

@@ -250,6 +250,7 @@ __global__ void build_tables_kernel(TableArgs t) {
 struct CompactArgs {
   const double2* full;
   double* q;
+  float* q32;  // or NULL
   int real, ncoef;
   int64_t Ny, nzh, nqy, nq, nmode;
 };
@@ -264,6 +265,10 @@ __global__ void compact_tables_kernel(CompactArgs c) {
     const double2 v = c.full[k * c.nmode + m];
     if (c.real) c.q[k * c.nq + e] = v.x;
     else reinterpret_cast<double2*>(c.q)[k * c.nq + e] = v;
+    if (c.q32) {
+      if (c.real) c.q32[k * c.nq + e] = (float)v.x;
+      else reinterpret_cast<float2*>(c.q32)[k * c.nq + e] = make_float2((float)v.x, (float)v.y);
+    }
   }
 }
 
@@ -442,7 +447,16 @@ __global__ void __launch_bounds__(256) update_quad_kernel(UpdArgs<C> u) {
   constexpr int ncf = VAR == 2 ? COEF_COUNT : COEF_PSI1;
 #pragma unroll
   for (int k = 0; k < ncf; ++k) {
-    if (REAL) {
+    if (sizeof(C) == 8 && u.coef.q32) {  // FP32 form: the tables' FP32 copy (same rounded values)
+      if (REAL) {
+        cf[k].x = __ldg(u.coef.q32 + k * u.coef.nq + e);
+        cf[k].y = 0;
+      } else {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(u.coef.q32) + k * u.coef.nq + e);
+        cf[k].x = v.x;
+        cf[k].y = v.y;
+      }
+    } else if (REAL) {
       cf[k].x = (decltype(C().x))__ldg(u.coef.q + k * u.coef.nq + e);
       cf[k].y = 0;
     } else {
@@ -788,6 +802,7 @@ pic_status psatd_setup(pic_ctx* ctx) {
   PIC_LAUNCH_CHECK(ctx);
   // compact tables for the step's update (see pic_ctx::coefq)
   ctx->coefq = nullptr;
+  ctx->coefq32 = nullptr;
   if (ctx->variant == PIC_PSATD_STANDARD || (ctx->vg[0] == 0.0 && ctx->vg[1] == 0.0)) {
     ctx->coefq_real = ctx->variant == PIC_PSATD_STANDARD ? 1 : 0;
     ctx->nqx = ctx->N[0] / 2 + 1;
@@ -795,9 +810,11 @@ pic_status psatd_setup(pic_ctx* ctx) {
     ctx->nq = ctx->nqx * ctx->nqy * ctx->nzh;
     const size_t words = (size_t)ctx->ncoef * ctx->nq * (ctx->coefq_real ? 1 : 2);
     PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->coefq, words * sizeof(double)));
+    if (ctx->precision == PIC_FP32) PIC_CUDA_TRY(ctx, cudaMalloc(&ctx->coefq32, words * sizeof(float)));
     CompactArgs c;
     c.full = ctx->coef;
     c.q = ctx->coefq;
+    c.q32 = ctx->coefq32;
     c.real = ctx->coefq_real;
     c.ncoef = ctx->ncoef;
     c.Ny = ctx->N[1];

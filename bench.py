@@ -43,8 +43,8 @@ HBM_PEAK_FALLBACK = 6800.0
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of the push stage per step (every species' push32_tile launch), from one
 # ncu capture of the current kernel version: at the full laser-wakefield size, and for the
-# beam-driven box on a 128 x 128 x 512 box of the same physics scaled by particles and cells
-# (profiles/push32_tile_*_dram.md); other workloads / forms report null
+# beam-driven box on a 128 x 128 x 512 box of the same physics scaled by 8 (particles and cells);
+# other workloads / forms report null
 MEASURED_TRAFFIC = {("beam_wakefield", (256, 256, 1024), "fp32"): 7.626e9,
                     ("laser_wakefield", (128, 128, 512), "fp32"): 1.496e9}
 # LSU data-pipe wavefronts (shared memory, L1, global) of the push stage per step, same captures:

@@ -433,12 +433,16 @@ size_t z_pipe_smem(int lgM, bool c2r) {
   return (size_t)(stage + L * zline_len(M)) * sizeof(float2);
 }
 
-// the persistent z passes run when every array they copy in bulk starts 16-byte aligned (the
-// staging copies of a tile start at a multiple of 16 bytes from it, and move whole 16-byte units:
-// the line count is even)
+int z_lines_per_cta(int Nz) { return kZTile / (Nz / 2); }
+
+// the persistent z passes run when every array they copy in bulk starts 16-byte aligned and every
+// tile's copy starts and ends on a 16-byte boundary: a complex line holds Nz/2 + 1 elements of 8
+// bytes, an odd multiple of 8 bytes, so the lines per tile and the total line count must be even
+// (an odd tile of C2R input would start 8 bytes off the boundary: a misaligned bulk copy)
 template <class P>
 bool z_pipe_ok(const pic_ctx* ctx, P const* p, int ncomp) {
   if (!ctx->dev_err || ctx->nsm <= 0 || (ctx->N[0] * ctx->N[1]) % 2 != 0) return false;
+  if (z_lines_per_cta((int)ctx->N[2]) % 2 != 0) return false;
   for (int c = 0; c < ncomp; ++c)
     if (reinterpret_cast<uintptr_t>(p[c]) % 16 != 0) return false;
   return true;
@@ -473,7 +477,6 @@ pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp)
   return PIC_OK;
 }
 
-int z_lines_per_cta(int Nz) { return kZTile / (Nz / 2); }
 
 template <class T>
 pic_status set_smem_attrs(pic_ctx* ctx) {

@@ -132,7 +132,7 @@ void pic_ext_default(pic_ext* e) {
 
 void pic_destroy(pic_ctx* ctx) {
   if (!ctx) return;
-  void* ptrs[] = {ctx->k1d, ctx->twid[0], ctx->twid[1], ctx->twid[2], ctx->coef, ctx->EBh,
+  void* ptrs[] = {ctx->k1d, ctx->twid[0], ctx->twid[1], ctx->twid[2], ctx->twid32[0], ctx->twid32[1], ctx->twid32[2], ctx->twp, ctx->twp32, ctx->coef, ctx->EBh,
                   ctx->rhoh[0], ctx->Jh, ctx->G, ctx->nodal, ctx->Jn, ctx->bin_tid, ctx->bin_counts,
                   ctx->bin_cursor, ctx->bin_tmp, ctx->cell_counts, ctx->cell_cursor, ctx->adj_work, ctx->bin_gate,
                   ctx->bin_outside, ctx->flt1d, ctx->bin_flags, ctx->k1d32, ctx->flt32, ctx->coefq,

@@ -34,7 +34,7 @@ using namespace pic_fft;
 template <class T, int LGM>
 __global__ void __launch_bounds__(kZThreads, (sizeof(T) == 4 ? 1536 : 1024) / kZThreads)
     fft_z_r2c_kernel(CRP6<T> in, CP6<typename Cplx<T>::type> out, int64_t nlines,
-                     const typename Cplx<T>::type* __restrict__ tw) {
+                     const typename Cplx<T>::type* __restrict__ tw, const typename Cplx<T>::type* __restrict__ twp) {
   using C = typename Cplx<T>::type;
   constexpr int M = 1 << LGM, L = kZTile / M, lgnb = LGM - 3, nb = 1 << lgnb;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kZThreads, (sizeof(T) == 4 ? 1536 : 1024) / kZ
     for (int r = 0; r < 8; ++r) v[r] = line < nlines ? src[r * nb] : czero<C>();
     pass0_from_regs<false>(sm, lay, v, j, l);
   }
-  passes_ct<false, LGM, 1, Plan<LGM>::npass>(sm, lay, tw, 2);
+  passes_ct<false, LGM, 1, Plan<LGM>::npass>(sm, lay, twp);
   // split: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W^k (Z_k - conj Z_{M-k}),  W = exp(-2 pi i / Nz)
   C* dst = out.p[comp];
   constexpr int nzh = M + 1, lgH = LGM - 1;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kZThreads, (sizeof(T) == 4 ? 1536 : 1024) / kZ
 template <class T, int LGM>
 __global__ void __launch_bounds__(kZThreads, (sizeof(T) == 4 ? 1536 : 1024) / kZThreads)
     fft_z_c2r_kernel(CP6<typename Cplx<T>::type> in, RP6<T> out, int64_t nlines,
-                     const typename Cplx<T>::type* __restrict__ tw) {
+                     const typename Cplx<T>::type* __restrict__ tw, const typename Cplx<T>::type* __restrict__ twp) {
   using C = typename Cplx<T>::type;
   constexpr int M = 1 << LGM, L = kZTile / M;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(kZThreads, (sizeof(T) == 4 ? 1536 : 1024) / kZ
     if (k != 0 && k != M - k) sm[lay.idx(M - k, l)] = cadd(cconj(A), cmuli(cmul(w, cconj(D))));
   }
   __syncthreads();
-  passes_ct<true, LGM, 0, Plan<LGM>::npass - 1>(sm, lay, tw, 2);
+  passes_ct<true, LGM, 0, Plan<LGM>::npass - 1>(sm, lay, twp);
   C* dst = reinterpret_cast<C*>(out.p[comp]) + line0 * M;
   const int nvalid = (int)min((int64_t)L, nlines - line0);
-  last_pass_to<true, LGM>(sm, lay, tw, 2, [&](int l, int e, C v) {
+  last_pass_to<true, LGM>(sm, lay, twp, [&](int l, int e, C v) {
     if (l < nvalid) dst[l * M + e] = v;
   });
 }
@@ -181,7 +181,8 @@ __device__ __forceinline__ bool zpipe_wait(uint64_t* bar, int i, int* err) {
 
 template <int LGM>
 __global__ void __launch_bounds__(kZThreads, kZPipeCtasPerSm)
-    fft_z_r2c_pipe_kernel(CRP6<float> in, CP6<float2> out, ZPipe zp, const float2* __restrict__ tw) {
+    fft_z_r2c_pipe_kernel(CRP6<float> in, CP6<float2> out, ZPipe zp, const float2* __restrict__ tw,
+                          const float2* __restrict__ twp) {
   using C = float2;
   constexpr int M = 1 << LGM, L = kZTile / M, lgnb = LGM - 3, nb = 1 << lgnb;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kZThreads, kZPipeCtasPerSm)
     __syncthreads();  // the staging buffer is free: fetch the next tile behind this one's passes
     if (threadIdx.x == 0 && t + (int)gridDim.x < zp.ntiles) zpipe_issue<C, L>(zp, src, M, t + gridDim.x, stage, &bar);
     pass0_from_regs<false>(sm, lay, v, j0, l0);
-    passes_ct<false, LGM, 1, Plan<LGM>::npass>(sm, lay, tw, 2);
+    passes_ct<false, LGM, 1, Plan<LGM>::npass>(sm, lay, twp);
     // split: X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W^k (Z_k - conj Z_{M-k}),  W = exp(-2 pi i / Nz)
     C* dst = out.p[comp];
     constexpr int nzh = M + 1, lgH = LGM - 1;
@@ -235,7 +236,8 @@ __global__ void __launch_bounds__(kZThreads, kZPipeCtasPerSm)
 
 template <int LGM>
 __global__ void __launch_bounds__(kZThreads, kZPipeCtasPerSm)
-    fft_z_c2r_pipe_kernel(CP6<float2> in, RP6<float> out, ZPipe zp, const float2* __restrict__ tw) {
+    fft_z_c2r_pipe_kernel(CP6<float2> in, RP6<float> out, ZPipe zp, const float2* __restrict__ tw,
+                          const float2* __restrict__ twp) {
   using C = float2;
   constexpr int M = 1 << LGM, L = kZTile / M, nzh = M + 1, P = M / 2 + 1, lgH = LGM - 1;
   constexpr int kBatch = (L * P + kZThreads - 1) / kZThreads;
@@ -285,9 +287,9 @@ __global__ void __launch_bounds__(kZThreads, kZPipeCtasPerSm)
     }
     __syncthreads();  // the staging buffer is free: fetch the next tile behind this one's passes
     if (threadIdx.x == 0 && t + (int)gridDim.x < zp.ntiles) zpipe_issue<C, L>(zp, src, nzh, t + gridDim.x, stage, &bar);
-    passes_ct<true, LGM, 0, Plan<LGM>::npass - 1>(sm, lay, tw, 2);
+    passes_ct<true, LGM, 0, Plan<LGM>::npass - 1>(sm, lay, twp);
     float2* dst = reinterpret_cast<float2*>(out.p[comp]) + line0 * M;
-    last_pass_to<true, LGM>(sm, lay, tw, 2, [&](int l, int e, C v) {
+    last_pass_to<true, LGM>(sm, lay, twp, [&](int l, int e, C v) {
       if (l < nvalid) dst[l * M + e] = v;
     });
     __syncthreads();  // the working tile is read before the next tile's pre-processing writes it
@@ -307,7 +309,7 @@ struct StridedMinBlocks {
 
 template <bool INV, class C, int LGN, int LGW>
 __global__ void __launch_bounds__((1 << (LGN + LGW)) / 8, (StridedMinBlocks<(1 << (LGN + LGW)) / 8, sizeof(C)>::value))
-    fft_strided_kernel(CP6<C> data, int64_t es, int64_t os, int ncols, const C* __restrict__ tw) {
+    fft_strided_kernel(CP6<C> data, int64_t es, int64_t os, int ncols, const C* __restrict__ twp) {
   constexpr int N = 1 << LGN, W = 1 << LGW, nb = N / 8;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -331,8 +333,8 @@ __global__ void __launch_bounds__((1 << (LGN + LGW)) / 8, (StridedMinBlocks<(1 <
     }
   } else {
     pass0_from_regs<INV>(sm, lay, v, j, w);
-    passes_ct<INV, LGN, 1, Plan<LGN>::npass - 1>(sm, lay, tw, 1);
-    last_pass_to<INV, LGN>(sm, lay, tw, 1, [&](int l, int e, C val) {
+    passes_ct<INV, LGN, 1, Plan<LGN>::npass - 1>(sm, lay, twp);
+    last_pass_to<INV, LGN>(sm, lay, twp, [&](int l, int e, C val) {
       if (l < wv) base[e * es + l] = val;
     });
   }
@@ -366,9 +368,11 @@ StridedFn<C> strided_fn(int lgN) {
 }
 
 template <class T>
-using ZR2CFn = void (*)(CRP6<T>, CP6<typename Cplx<T>::type>, int64_t, const typename Cplx<T>::type*);
+using ZR2CFn = void (*)(CRP6<T>, CP6<typename Cplx<T>::type>, int64_t, const typename Cplx<T>::type*,
+                        const typename Cplx<T>::type*);
 template <class T>
-using ZC2RFn = void (*)(CP6<typename Cplx<T>::type>, RP6<T>, int64_t, const typename Cplx<T>::type*);
+using ZC2RFn = void (*)(CP6<typename Cplx<T>::type>, RP6<T>, int64_t, const typename Cplx<T>::type*,
+                        const typename Cplx<T>::type*);
 
 // the z kernels for M = Nz / 2 = 2^lgM (8 <= M <= 512)
 template <class T>
@@ -398,8 +402,8 @@ ZC2RFn<T> z_c2r_fn(int lgM) {
   return nullptr;
 }
 
-using ZR2CPipeFn = void (*)(CRP6<float>, CP6<float2>, ZPipe, const float2*);
-using ZC2RPipeFn = void (*)(CP6<float2>, RP6<float>, ZPipe, const float2*);
+using ZR2CPipeFn = void (*)(CRP6<float>, CP6<float2>, ZPipe, const float2*, const float2*);
+using ZC2RPipeFn = void (*)(CP6<float2>, RP6<float>, ZPipe, const float2*, const float2*);
 
 ZR2CPipeFn z_r2c_pipe_fn(int lgM) {
   switch (lgM) {
@@ -451,6 +455,9 @@ bool z_pipe_ok(const pic_ctx* ctx, P const* p, int ncomp) {
 template <class C> const C* twiddles(const pic_ctx* ctx, int a);
 template <> const double2* twiddles<double2>(const pic_ctx* ctx, int a) { return ctx->twid[a]; }
 template <> const float2* twiddles<float2>(const pic_ctx* ctx, int a) { return ctx->twid32[a]; }
+template <class C> const C* pass_twiddles(const pic_ctx* ctx);
+template <> const double2* pass_twiddles<double2>(const pic_ctx* ctx) { return ctx->twp; }
+template <> const float2* pass_twiddles<float2>(const pic_ctx* ctx) { return ctx->twp32; }
 
 template <class C>
 pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp) {
@@ -472,7 +479,7 @@ pic_status launch_strided(pic_ctx* ctx, CP6<C> d, int axis, bool inv, int ncomp)
   if (!fn) return pic_set_error(ctx, PIC_ERR_UNSUPPORTED, "transform length %d", N);
   dim3 grid((nzh + W - 1) / W, (unsigned)nouter, ncomp);
   const size_t smem = N > 8 ? (size_t)W * N * sizeof(C) : 0;
-  fn<<<grid, W * N / 8, smem, ctx->stream>>>(d, es, os, nzh, twiddles<C>(ctx, axis));
+  fn<<<grid, W * N / 8, smem, ctx->stream>>>(d, es, os, nzh, pass_twiddles<C>(ctx));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }
@@ -545,6 +552,30 @@ pic_status fft_setup(pic_ctx* ctx) {
     delete[] hf;
     if (e != cudaSuccess) return pic_set_error(ctx, PIC_ERR_NOMEM, "twiddle table: %s", cudaGetErrorString(e));
   }
+  {
+    // per-pass tables (see pass_twiddle_offset): [r - 1][k] = exp(-2 pi i k r / (Ns R))
+    double2* h = new double2[kPassTwiddles];
+    float2* hf = new float2[kPassTwiddles];
+    for (int lgNs = 3; lgNs <= 9; lgNs += 3) {
+      for (int lgR = 3; lgR >= 1; --lgR) {
+        const int Ns = 1 << lgNs, R = 1 << lgR, off = pass_twiddle_offset(lgNs, lgR);
+        for (int r = 1; r < R; ++r)
+          for (int k = 0; k < Ns; ++k) {
+            double sn, cs;
+            sincospi_frac(2 * (int64_t)k * r, (int64_t)Ns * R, &sn, &cs);
+            h[off + (r - 1) * Ns + k] = make_double2(cs, -sn);
+            hf[off + (r - 1) * Ns + k] = make_float2((float)cs, (float)-sn);
+          }
+      }
+    }
+    cudaError_t e = cudaMalloc(&ctx->twp, kPassTwiddles * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twp, h, kPassTwiddles * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->twp32, kPassTwiddles * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->twp32, hf, kPassTwiddles * sizeof(float2), cudaMemcpyHostToDevice);
+    delete[] h;
+    delete[] hf;
+    if (e != cudaSuccess) return pic_set_error(ctx, PIC_ERR_NOMEM, "twiddle table: %s", cudaGetErrorString(e));
+  }
   pic_status st = set_smem_attrs<double>(ctx);
   if (st != PIC_OK) return st;
   return set_smem_attrs<float>(ctx);
@@ -564,7 +595,8 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
       const ZPipe zp{nlines, tpc, tpc * ncomp, ctx->dev_err};
       const int grid = std::min(zp.ntiles, kZPipeCtasPerSm * ctx->nsm);
       z_r2c_pipe_fn(lgM)<<<grid, kZThreads, z_pipe_smem(lgM, false), ctx->stream>>>(in, out, zp,
-                                                                                     twiddles<C>(ctx, 2));
+                                                                                     twiddles<C>(ctx, 2),
+                                                                                     pass_twiddles<C>(ctx));
       PIC_LAUNCH_CHECK(ctx);
       pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
       if (st != PIC_OK) return st;
@@ -573,7 +605,8 @@ pic_status fft_r2c(pic_ctx* ctx, CRP6<T> in, CP6<typename Cplx<T>::type> out, in
   }
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  z_r2c_fn<T>(lgM)<<<grid, kZThreads, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
+  z_r2c_fn<T>(lgM)<<<grid, kZThreads, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2),
+                                                            pass_twiddles<C>(ctx));
   PIC_LAUNCH_CHECK(ctx);
   pic_status st = launch_strided<C>(ctx, out, 1, false, ncomp);
   if (st != PIC_OK) return st;
@@ -598,14 +631,16 @@ pic_status fft_c2r(pic_ctx* ctx, CP6<typename Cplx<T>::type> in, RP6<T> out, int
       const ZPipe zp{nlines, tpc, tpc * ncomp, ctx->dev_err};
       const int grid = std::min(zp.ntiles, kZPipeCtasPerSm * ctx->nsm);
       z_c2r_pipe_fn(lgM)<<<grid, kZThreads, z_pipe_smem(lgM, true), ctx->stream>>>(in, out, zp,
-                                                                                    twiddles<C>(ctx, 2));
+                                                                                    twiddles<C>(ctx, 2),
+                                                                                    pass_twiddles<C>(ctx));
       PIC_LAUNCH_CHECK(ctx);
       return PIC_OK;
     }
   }
   dim3 grid((unsigned)((nlines + L - 1) / L), ncomp);
   const size_t smem = (size_t)L * zline_len(Nz / 2) * sizeof(C);
-  z_c2r_fn<T>(lgM)<<<grid, kZThreads, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2));
+  z_c2r_fn<T>(lgM)<<<grid, kZThreads, smem, ctx->stream>>>(in, out, nlines, twiddles<C>(ctx, 2),
+                                                            pass_twiddles<C>(ctx));
   PIC_LAUNCH_CHECK(ctx);
   return PIC_OK;
 }

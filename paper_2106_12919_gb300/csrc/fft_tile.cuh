@@ -88,11 +88,21 @@ __device__ __forceinline__ void dft(C* v) {
   }
 }
 
+// Per-pass twiddle tables.  Pass (Ns, R) multiplies input r of butterfly k < Ns by
+// w^{k r}, w = exp(-2 pi i / (Ns R)): a function of (Ns, R) only, not of the transform length.  One
+// table holds every pass of every length up to 1024, r-major ([r - 1][k]), so the lanes of a warp,
+// which hold consecutive k, read consecutive entries: one or two 128-byte lines per load, where
+// the length-N table read at stride (N / (Ns R)) r spread a warp's loads over up to 28 lines.
+// Sections for Ns = 8, 64, 512, each R = 8, 4, 2 (7, 3, 1 entries per k).
+constexpr int kPassTwiddles = 6424;  // sum over Ns of 11 Ns
+__host__ __device__ __forceinline__ constexpr int pass_twiddle_offset(int lgNs, int lgR) {
+  return 11 * ((1 << lgNs) - 8) / 7 + (lgR == 3 ? 0 : (lgR == 2 ? 7 : 10)) * (1 << lgNs);
+}
+
 // One Stockham pass of radix R on all lines of the tile, in place.  The CTA has
-// exactly L * N / 8 threads; each thread handles 8 / R butterflies.
+// exactly L * N / 8 threads; each thread handles 8 / R butterflies.  twp: the per-pass tables.
 template <int R, bool INV, class C, class LAY>
-__device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int lgN, int lgNs, const C* __restrict__ tw,
-                                              int twstride) {
+__device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int lgN, int lgNs, const C* __restrict__ twp) {
   constexpr int PER = 8 / R;
   constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
   const int T = blockDim.x;
@@ -116,10 +126,10 @@ __device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int lgN, int
     const int j = oj[q], l = ol[q];
     const int k = j & (Ns - 1);
     if (Ns > 1) {
-      const int step = k << (lgN - lgNs - LGR);  // (N / (Ns R)) k
+      const C* t = twp + pass_twiddle_offset(lgNs, LGR) + k;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        C w = __ldg(&tw[step * r * twstride]);
+        C w = __ldg(&t[(r - 1) * Ns]);
         if (INV) w.y = -w.y;
         v[q][r] = cmul(v[q][r], w);
       }
@@ -132,18 +142,6 @@ __device__ __forceinline__ void stockham_pass(C* s, const LAY& lay, int lgN, int
   __syncthreads();
 }
 
-template <bool INV, class C, class LAY>
-__device__ void fft_tile(C* s, const LAY& lay, int N, const C* __restrict__ tw, int twstride) {
-  const int lgN = lg2(N);
-  int lgNs = 0, rem = lgN;
-  while (rem >= 3) {
-    stockham_pass<8, INV>(s, lay, lgN, lgNs, tw, twstride);
-    lgNs += 3;
-    rem -= 3;
-  }
-  if (rem == 2) stockham_pass<4, INV>(s, lay, lgN, lgNs, tw, twstride);
-  else if (rem == 1) stockham_pass<2, INV>(s, lay, lgN, lgNs, tw, twstride);
-}
 
 // ---------------------------------------------------------------------------
 // Transforms of a compile-time length N = 2^LGN: radix-8 passes p = 0, 1, ... (Ns = 8^p) and one
@@ -164,10 +162,10 @@ struct PassLgR {
 
 // passes P .. PEND - 1, shared memory to shared memory
 template <bool INV, int LGN, int P, int PEND, class C, class LAY>
-__device__ __forceinline__ void passes_ct(C* s, const LAY& lay, const C* __restrict__ tw, int twstride) {
+__device__ __forceinline__ void passes_ct(C* s, const LAY& lay, const C* __restrict__ twp) {
   if constexpr (P < PEND) {
-    stockham_pass<1 << PassLgR<LGN, P>::value, INV>(s, lay, LGN, 3 * P, tw, twstride);
-    passes_ct<INV, LGN, P + 1, PEND>(s, lay, tw, twstride);
+    stockham_pass<1 << PassLgR<LGN, P>::value, INV>(s, lay, LGN, 3 * P, twp);
+    passes_ct<INV, LGN, P + 1, PEND>(s, lay, twp);
   }
 }
 
@@ -183,8 +181,7 @@ __device__ __forceinline__ void pass0_from_regs(C* s, const LAY& lay, C (&v)[8],
 
 // the last pass (Ns = N / R), from shared memory; out(l, e, value) receives element e of line l
 template <bool INV, int LGN, class C, class LAY, class OUT>
-__device__ __forceinline__ void last_pass_to(const C* s, const LAY& lay, const C* __restrict__ tw, int twstride,
-                                             OUT&& out) {
+__device__ __forceinline__ void last_pass_to(const C* s, const LAY& lay, const C* __restrict__ twp, OUT&& out) {
   constexpr int P = Plan<LGN>::npass - 1;
   constexpr int LGR = PassLgR<LGN, P>::value;
   constexpr int R = 1 << LGR, PER = 8 / R;
@@ -205,9 +202,10 @@ __device__ __forceinline__ void last_pass_to(const C* s, const LAY& lay, const C
   for (int q = 0; q < PER; ++q) {
     const int k = oj[q];  // j < Ns: the butterfly's twiddle index and its first output
     if (P > 0) {
+      const C* t = twp + pass_twiddle_offset(3 * P, LGR) + k;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        C w = __ldg(&tw[k * r * twstride]);
+        C w = __ldg(&t[(r - 1) * nb]);
         if (INV) w.y = -w.y;
         v[q][r] = cmul(v[q][r], w);
       }

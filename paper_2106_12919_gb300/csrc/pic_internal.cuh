@@ -108,6 +108,8 @@ struct pic_ctx {
   float* flt32;      // FP32 copy of flt1d
   double2* twid[3];  // twiddles exp(-2 pi i j / N_a), j < N_a
   float2* twid32[3]; // the same rounded to FP32
+  double2* twp;      // per-pass twiddles of the transform passes (fft_tile.cuh), and in FP32
+  float2* twp32;
   double2* coef;     // [ncoef][nmode]
   // Compact copy of the tables read by the step's update (NULL when v_gal has a transverse
   // component): the coefficients depend on k_x, k_y through [k_x]_s^2, [k_y]_s^2 only, so the

@@ -805,16 +805,24 @@ size_t chunk_map_offset(const pic_ctx* ctx) {
   return (size_t)ctx->n_tiles + 1 + (size_t)((ctx->n_tiles + kScanBlock - 1) / kScanBlock) + 1;
 }
 
-// smallest stride >= v that is 8 (mod 32) words
-int pad_plane(int v) { return v + (((8 - v) % 32) + 32) % 32; }
+// smallest stride >= v that is 8 or 24 (mod 32) words: a warp's lanes (8 z cells x 4 x planes)
+// then fall on 32 distinct banks (z + 8 x or z + 24 x, mod 32)
+int pad_plane(int v) {
+  const int a = v + (((8 - v) % 32) + 32) % 32, b = v + (((24 - v) % 32) + 32) % 32;
+  return std::min(a, b);
+}
 
-// tile geometry and shared-memory strides of the tiled push; returns the dynamic shared bytes
-size_t tile_layout(const pic_ctx* ctx, TileArgs& t) {
+// tile geometry and shared-memory strides of the tiled push; returns the dynamic shared bytes.
+// The window spans the tile, 2 nodes before it and 3 after it on every axis (the cubic block of a
+// particle one cell past the tile), except 2 after it along x when wx_after = 2 (see
+// launch_push32_tiled): a particle that moved past the tile's upper x face since its binning then
+// deposits through global memory.
+size_t tile_layout(const pic_ctx* ctx, TileArgs& t, int wx_after) {
   t.cpt = 1;
   for (int d = 0; d < 3; ++d) {
     t.T[d] = ctx->tile[d];
     t.nt[d] = (int)(ctx->N[d] / ctx->tile[d]);
-    t.W[d] = ctx->tile[d] + 5;
+    t.W[d] = ctx->tile[d] + (d == 0 ? 2 + wx_after : 5);
     t.G[d] = ctx->tile[d] + 3;
     t.cpt *= ctx->tile[d];
   }
@@ -833,18 +841,30 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
   t.chunk_tile = chunk + chunk_map_offset(ctx);
   t.n_tiles = ctx->n_tiles;
   t.outside = ctx->bin_outside;
-  const size_t smem = tile_layout(ctx, t);
+  // the window one node shorter along x when that lets more CTAs share an SM (e.g. 8 x 16 x 8
+  // tiles: 3 -> 4 CTAs, the register limit)
+  size_t smem = tile_layout(ctx, t, 3);
+  {
+    TileArgs t2 = t;
+    const size_t smem2 = tile_layout(ctx, t2, 2);
+    const void* fn = ctx->shape_order == 1 ? (const void*)push32_tile_kernel<1>
+                     : ctx->shape_order == 2 ? (const void*)push32_tile_kernel<2>
+                                             : (const void*)push32_tile_kernel<3>;
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int n3 = 0, n2 = 0;
+    PIC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, fn, kTileThreads, smem));
+    PIC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, fn, kTileThreads, smem2));
+    if (n2 > n3) {
+      t = t2;
+      smem = smem2;
+    }
+  }
   bool aligned = ctx->N[2] % 4 == 0;
   const float* dsts[4] = {a.J[0], a.J[1], a.J[2], a.rho};
   for (const float* d : dsts) aligned = aligned && (reinterpret_cast<uintptr_t>(d) % 16 == 0);
   t.vec_flush = aligned ? 1 : 0;
   // sum over tiles of ceil(count / kTileChunk) < n_tiles + n / kTileChunk: surplus CTAs return at once
   const unsigned nb = (unsigned)(ctx->n_tiles + (a.n + kTileChunk - 1) / kTileChunk);
-  if (smem > 48 * 1024) {
-    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(push32_tile_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
   switch (ctx->shape_order) {
     case 1: push32_tile_kernel<1><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
     case 2: push32_tile_kernel<2><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
@@ -1301,7 +1321,7 @@ int bin32_launches(const pic_ctx* ctx, int64_t n, bool chunks, bool copy_back) {
 
 bool tiled_push_fits(const pic_ctx* ctx) {
   TileArgs t;
-  return tile_layout(ctx, t) <= 160 * 1024 && ctx->ncell < (int64_t(1) << 31);
+  return tile_layout(ctx, t, 3) <= 160 * 1024 && ctx->ncell < (int64_t(1) << 31);
 }
 
 size_t tile_chunk_words(const pic_ctx* ctx, int64_t n) {

@@ -1201,7 +1201,13 @@ __global__ void tile_scatter_kernel(TileScatterArgs a) {
   if (gated_off(a.gate)) return;
   a.k = load_frame(a.k);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.k.n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int t = key_of(a.k, (int)a.spc[0][p]) >> a.k.cpt_shift;
+    // the particle's words are loaded before the cursor atomic (which the compiler may not move
+    // them past), so their latency overlaps it
+    uint32_t v[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) v[f] = a.spc[f][p];
+    const unsigned long long id = a.id_spc ? a.id_spc[p] : 0ull;
+    const int t = key_of(a.k, (int)v[0]) >> a.k.cpt_shift;
     const unsigned active = __activemask();
     const unsigned peers = __match_any_sync(active, t);
     const int lane = threadIdx.x & 31;
@@ -1212,8 +1218,8 @@ __global__ void tile_scatter_kernel(TileScatterArgs a) {
     base = __shfl_sync(peers, base, leader);
     const int64_t q = (int64_t)a.off[t] + base + rank;
 #pragma unroll
-    for (int f = 0; f < 8; ++f) a.tmp[f][q] = a.spc[f][p];
-    if (a.id_spc) a.id_tmp[q] = a.id_spc[p];
+    for (int f = 0; f < 8; ++f) a.tmp[f][q] = v[f];
+    if (a.id_spc) a.id_tmp[q] = id;
   }
 }
 
@@ -1258,11 +1264,15 @@ __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(TileScatterAr
     __syncthreads();
     for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) {
       const int64_t j = b0 + i;
-      const int l = key_of(a.k, (int)a.tmp[0][j]) & lmask;
+      uint32_t v[8];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) v[f] = a.tmp[f][j];
+      const unsigned long long id = a.id_spc ? a.id_tmp[j] : 0ull;
+      const int l = key_of(a.k, (int)v[0]) & lmask;
       const int64_t q = b0 + atomicAdd(&cnt[l], 1u);
 #pragma unroll
-      for (int f = 0; f < 8; ++f) a.spc[f][q] = a.tmp[f][j];
-      if (a.id_spc) a.id_spc[q] = a.id_tmp[j];
+      for (int f = 0; f < 8; ++f) a.spc[f][q] = v[f];
+      if (a.id_spc) a.id_spc[q] = id;
     }
     __syncthreads();  // cnt is reused by the next tile
   }

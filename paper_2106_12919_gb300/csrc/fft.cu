@@ -14,7 +14,9 @@
 // npass passes goes through shared memory npass - 1 times.  z lines are contiguous (line-major
 // tile, padded one slot per 16 elements to spread the radix-8 scatter over the banks); y and x
 // lines are strided, so a CTA takes W adjacent columns (consecutive k_z) and the tile is
-// element-major, which keeps the global loads coalesced in W-element rows.
+// element-major, which keeps the global loads coalesced in W-element rows.  The passes read their
+// twiddles from per-pass tables (fft_tile.cuh).  In the FP32 form the z passes run as persistent
+// kernels whose next tile arrives by a bulk copy while the current one is transformed.
 #include "pic_internal.cuh"
 #include "fft_tile.cuh"
 

@@ -204,6 +204,9 @@ def test_step32_without_J(cycle):
 CASES = [
     ("laser_wakefield", dict(shape=(16, 16, 64), ppc=1), 100, False),
     ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 100, False),
+    # 8 x 16 x 8 tiles (the bench's beam-driven tiles): their deposit window is one node shorter
+    # along x so that 4 CTAs share an SM; a particle past a tile's upper x face deposits globally
+    ("beam_wakefield:tile8168", dict(shape=(16, 16, 64), ppc=1, n_beam=500), 100, False),
     # a dense driver: its central tiles hold up to ~5000 particles, so the tiled push
     # splits them into chunks of at most 2048 that deposit into the same tile window
     ("beam_wakefield", dict(shape=(16, 16, 64), ppc=1, n_beam=100000), 20, False),
@@ -297,7 +300,8 @@ def test_fp32_step_within_1e5_of_fp64_oracle(name, kw, nsteps, chaotic):
         half = 0.5 * shape[2] * dx[2]
         w["species"] = [{k: (v[s["z"] < half] if isinstance(v, np.ndarray) else v) for k, v in s.items()}
                         for s in w["species"]]
-    ctx = ctx32(p, sort_interval=10, **opts)
+    tile = {"tile": (8, 16, 8)} if opt == "tile8168" else {}
+    ctx = ctx32(p, sort_interval=10, **tile, **opts)
     sp = species32(ctx, w["species"])
     op = step.Params(**p, **opts)
     E0 = [a.astype(np.float32).astype(np.float64) for a in w["E"]]

@@ -483,7 +483,9 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   const int G1 = t.G[1], G2 = t.G[2], gplane = t.gplane, gcomp = t.gcomp;
   // the staged fields are needed in phase 1 only and the deposit window in phase 2 only:
   // both live at the start of the dynamic shared memory
-  float* fld = smem;  // [6][G0][G1][G2], plane stride gplane
+  // [3][G0][G1][G2] pairs (E_x, E_y), (E_z, B_x), (B_y, B_z), plane stride gplane: one 8-byte load
+  // reads two components of a node
+  float2* fld = reinterpret_cast<float2*>(smem);
   const int go0 = tx * t.T[0] - 1 + fs[0], go1 = ty * t.T[1] - 1 + fs[1], go2 = tz * t.T[2] - 1 + fs[2];
   int p0, cnt, ppc;
   {
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     const int o = (((go0 + i) & a.mask[0]) * (int)a.Ny + ((go1 + j) & a.mask[1])) * (int)a.Nz + ((go2 + k) & a.mask[2]);
     const int d = i * gplane + j * G2 + k;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) fld[q * gcomp + d] = __ldg(a.F[q] + o);
+    for (int q = 0; q < 3; ++q) fld[q * gcomp + d] = make_float2(__ldg(a.F[2 * q] + o), __ldg(a.F[2 * q + 1] + o));
   }
   __syncthreads();
   constexpr int NS = P + 1;
@@ -560,12 +562,16 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
 #pragma unroll
         for (int jj = 0; jj < NS; ++jj) {
           const float sxy = Sx[i] * Sy[jj];
-          const float* row = fld + (gx + i) * gplane + (gy + jj) * G2 + gz;
+          const float2* row = fld + (gx + i) * gplane + (gy + jj) * G2 + gz;
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
             const float w = sxy * Sz[k];
 #pragma unroll
-            for (int qq = 0; qq < 6; ++qq) f[qq] += w * row[qq * gcomp + k];
+            for (int qq = 0; qq < 3; ++qq) {
+              const float2 v = row[qq * gcomp + k];
+              f[2 * qq] += w * v.x;
+              f[2 * qq + 1] += w * v.y;
+            }
           }
         }
       }

@@ -659,7 +659,9 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
   win.sj[2] = scale[2];
   win.sr = scale[3];
   // the staged fields are dead: clear the deposit window in their place
-  for (int e = threadIdx.x; e < 4 * t.wcomp; e += blockDim.x) smem[e] = 0.0f;
+  // (4 wcomp floats, wcomp a multiple of 8: 16-byte stores)
+  for (int e = threadIdx.x; e < t.wcomp; e += blockDim.x)
+    reinterpret_cast<float4*>(smem)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   // Phase 2: deposit J^{n+1/2} at the midpoint x^{n+1} - (dt/2)(v - v_gal) and rho^{n+1} at
   // x^{n+1}, from the state written in phase 1 (same thread, same particles).

@@ -319,7 +319,9 @@ pic_status pic_step32(pic_ctx* ctx, float* const E[3], float* const B[3], float*
           PIC_TRY32(particles_bin32(ctx, &sp[q], ctx->sp_off[q], ctx->bin_gate, ctx->sp_chunk[q], false,
                                     ctx->frame + 8 * q));
         }
-        StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? 1 : 0);
+        // on a grid moving along z two launches: the instantiation for the species' frame velocity
+        // works, its twin returns
+        StageScope t(ctx, STAGE_PUSH, sp[q].n > 0 ? (ctx->vg[2] != 0.0 ? 2 : 1) : 0);
         PIC_TRY32(particles_push32_tiled(ctx, En, Bn, &sp[q], Jnp, rho, ctx->sp_off[q], ctx->sp_chunk[q],
                                          bin32_two_level(ctx) ? nullptr : bin32_scatter_gate(ctx),
                                          ctx->frame + 8 * q, ctx->dhist + 10 * q));

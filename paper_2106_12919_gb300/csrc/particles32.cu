@@ -223,6 +223,73 @@ __device__ __forceinline__ bool deposit_window(const Push32Args& a, const Window
   return true;
 }
 
+// z start of a particle's shape block (its first node) relative to its cell
+template <int P>
+__device__ __forceinline__ int shape_base_offset(float f) {
+  return P == 2 ? (f >= 0.5f ? 0 : -1) : (P == 3 ? -1 : 0);
+}
+
+// J of one particle (cell (ix, iy, iz) + offsets: the current-deposit midpoint) over NS + 1 z nodes
+// from node lz0, its own block starting lz - lz0 = 0 or 1 nodes in and the other node taking 0; a
+// particle whose block starts elsewhere, or that leaves the window, deposits through global
+// memory.  With lz0 the lowest midpoint block start of the warp relative to the lanes' x^{n+1}
+// cells, the lanes address the window relative to those cells, whose pattern fills 32 distinct
+// banks: a plasma streaming through a Galilean grid shifts its midpoints by about half a cell,
+// which sends neighbouring lanes' per-particle blocks to the same node (bank conflicts that cost
+// 6.9 wavefronts per particle on the beam-driven box).  The integer contributions of the block's
+// nodes are those of deposit_window.
+template <int P>
+__device__ __forceinline__ void deposit_j5(const Push32Args& a, const Window& win, int ix, int iy, int iz, float fx,
+                                           float fy, float fz, float v0, float v1, float v2, int lz0) {
+  constexpr int NS = P + 1;
+  int lx, ly, lz;
+  float Sx[NS], Sy[NS], Sz[NS];
+  shape32<P>(ix, fx, lx, Sx);
+  shape32<P>(iy, fy, ly, Sy);
+  shape32<P>(iz, fz, lz, Sz);
+  const int sh = lz - lz0;
+  const int wx = (lx - win.org[0]) & a.mask[0], wy = (ly - win.org[1]) & a.mask[1],
+            wz = (lz0 - win.org[2]) & a.mask[2];
+  if (!((unsigned)sh <= 1u && wx + NS <= win.W[0] && wy + NS <= win.W[1] && wz + NS + 1 <= win.W[2])) {
+#pragma unroll 1
+    for (int i = 0; i < NS; ++i) {
+      const int ox = ((lx + i) & a.mask[0]) * (int)a.Ny;
+      const float sx = Sx[i];
+#pragma unroll
+      for (int jj = 0; jj < NS; ++jj) {
+        const int oy = (ox + ((ly + jj) & a.mask[1])) * (int)a.Nz;
+        const float sxy = sx * Sy[jj];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          const int o = oy + ((lz + k) & a.mask[2]);
+          const float s = sxy * Sz[k];
+          atomicAdd(a.J[0] + o, s * v0);
+          atomicAdd(a.J[1] + o, s * v1);
+          atomicAdd(a.J[2] + o, s * v2);
+        }
+      }
+    }
+    return;
+  }
+  const int comp = win.comp;
+  const float w0 = v0 * win.sj[0], w1 = v1 * win.sj[1], w2 = v2 * win.sj[2];
+#pragma unroll(P == 3 ? 1 : NS)
+  for (int i = 0; i < NS; ++i) {
+#pragma unroll
+    for (int jj = 0; jj < NS; ++jj) {
+      const float sxy = Sx[i] * Sy[jj];
+      int* row = win.acc + (wx + i) * win.plane + (wy + jj) * win.W[2] + wz;
+#pragma unroll
+      for (int k = 0; k <= NS; ++k) {
+        const float s = sxy * (sh ? (k > 0 ? Sz[k - 1] : 0.f) : (k < NS ? Sz[k] : 0.f));
+        atomicAdd(row + k, __float2int_rn(s * w0));
+        atomicAdd(row + comp + k, __float2int_rn(s * w1));
+        atomicAdd(row + 2 * comp + k, __float2int_rn(s * w2));
+      }
+    }
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) push32_kernel(Push32Args a) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -437,11 +504,45 @@ __device__ __forceinline__ int interleaved(int j, int q, int s) {
   return (j - r * q) * s + r;
 }
 
-template <int P>
+// phase 2 of the tiled push over the chunk's particles (see push32_tile_kernel)
+template <int P, bool JEXT>
+__device__ __forceinline__ void deposit_phase(const Push32Args& a, const Window& win, int p0, int cnt, int q, int s) {
+  for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
+    const int pr = interleaved(j, q, s);
+    if (pr >= cnt) continue;
+    const int p = p0 + pr;
+    const int c = a.cell[p];
+    const int nx = (c >> (a.shz + a.shy)) & a.mask[0], ny = (c >> a.shz) & a.mask[1], nz = c & a.mask[2];
+    const float nfx = a.fx[p], nfy = a.fy[p], nfz = a.fz[p];
+    const float ux = a.ux[p], uy = a.uy[p], uz = a.uz[p];
+    const float qw = a.w[p] * a.qw_scale;
+    const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
+    const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
+    const float hX = -0.5f * a.dtdx[0] * (vx - a.vg[0]), hY = -0.5f * a.dtdx[1] * (vy - a.vg[1]),
+                hZ = -0.5f * a.dtdx[2] * (vz - a.vg[2]);
+    float mfx, mfy, mfz;
+    const int mx = nx + move_offset(nfx, hX, mfx), my = ny + move_offset(nfy, hY, mfy),
+              mz = nz + move_offset(nfz, hZ, mfz);
+    if (JEXT) {
+      const int ozmin = __reduce_min_sync(__activemask(), mz - nz + shape_base_offset<P>(mfz));
+      deposit_j5<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, nz + ozmin);
+    } else {
+      deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
+    }
+    deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
+  }
+}
+
+
+// JEXT: the J deposit of deposit_phase.  On a grid moving along z a species with a tile frame gets
+// both instantiations launched, and the one that does not match its frame's z velocity (nonzero:
+// streaming through the grid) returns at once; elsewhere only JEXT = false is launched and runs.
+template <int P, bool JEXT>
 __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile_kernel(Push32Args a, TileArgs t) {
   extern __shared__ float smem[];
   __shared__ int s_tile, s_part;
   __shared__ float s_bnd[4][kTileThreads / 32];
+  if (a.vg[2] != 0.0f && (a.frame != nullptr && __ldg(a.frame + 6) != 0) != JEXT) return;
   if (threadIdx.x == 0) {
     // chunk blockIdx.x: its tile from the chunk map, its index within the tile from the chunk starts
     const uint32_t b = blockIdx.x;
@@ -664,26 +765,11 @@ __global__ void __launch_bounds__(kTileThreads, 1024 / kTileThreads) push32_tile
     reinterpret_cast<float4*>(smem)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   // Phase 2: deposit J^{n+1/2} at the midpoint x^{n+1} - (dt/2)(v - v_gal) and rho^{n+1} at
-  // x^{n+1}, from the state written in phase 1 (same thread, same particles).
-  for (int j = threadIdx.x; j < q * s; j += blockDim.x) {
-    const int pr = interleaved(j, q, s);
-    if (pr >= cnt) continue;
-    const int p = p0 + pr;
-    const int c = a.cell[p];
-    const int nx = (c >> (a.shz + a.shy)) & a.mask[0], ny = (c >> a.shz) & a.mask[1], nz = c & a.mask[2];
-    const float nfx = a.fx[p], nfy = a.fy[p], nfz = a.fz[p];
-    const float ux = a.ux[p], uy = a.uy[p], uz = a.uz[p];
-    const float qw = a.w[p] * a.qw_scale;
-    const float ig = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * a.inv_c2);
-    const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
-    const float hX = -0.5f * a.dtdx[0] * (vx - a.vg[0]), hY = -0.5f * a.dtdx[1] * (vy - a.vg[1]),
-                hZ = -0.5f * a.dtdx[2] * (vz - a.vg[2]);
-    float mfx, mfy, mfz;
-    const int mx = nx + move_offset(nfx, hX, mfx), my = ny + move_offset(nfy, hY, mfy),
-              mz = nz + move_offset(nfz, hZ, mfz);
-    deposit_window<P>(a, win, mx, my, mz, mfx, mfy, mfz, qw * vx, qw * vy, qw * vz, 0.f, true);
-    deposit_window<P>(a, win, nx, ny, nz, nfx, nfy, nfz, 0.f, 0.f, 0.f, qw, false);
-  }
+  // x^{n+1}, from the state written in phase 1 (same thread, same particles).  A species whose
+  // tile frame streams along z (frame velocity != 0: the particles cross a cell per step relative
+  // to the grid) deposits J over NS + 1 z nodes from the warp's lowest midpoint block
+  // (deposit_j5), the others one block per particle.
+  deposit_phase<P, JEXT>(a, win, p0, cnt, q, s);
   nout = __reduce_add_sync(0xffffffffu, nout);
   if (nout && (threadIdx.x & 31) == 0) atomicAdd(t.outside, (unsigned long long)nout);
   if (a.dhist) {
@@ -855,10 +941,14 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
   {
     TileArgs t2 = t;
     const size_t smem2 = tile_layout(ctx, t2, 2);
-    const void* fn = ctx->shape_order == 1 ? (const void*)push32_tile_kernel<1>
-                     : ctx->shape_order == 2 ? (const void*)push32_tile_kernel<2>
-                                             : (const void*)push32_tile_kernel<3>;
+    const void* fn = ctx->shape_order == 1 ? (const void*)push32_tile_kernel<1, false>
+                     : ctx->shape_order == 2 ? (const void*)push32_tile_kernel<2, false>
+                                             : (const void*)push32_tile_kernel<3, false>;
+    const void* fx = ctx->shape_order == 1 ? (const void*)push32_tile_kernel<1, true>
+                     : ctx->shape_order == 2 ? (const void*)push32_tile_kernel<2, true>
+                                             : (const void*)push32_tile_kernel<3, true>;
     PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PIC_CUDA_TRY(ctx, cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int n3 = 0, n2 = 0;
     PIC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, fn, kTileThreads, smem));
     PIC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, fn, kTileThreads, smem2));
@@ -874,11 +964,22 @@ pic_status launch_push32_tiled(pic_ctx* ctx, const Push32Args& a, const int64_t*
   // sum over tiles of ceil(count / kTileChunk) < n_tiles + n / kTileChunk: surplus CTAs return at once
   const unsigned nb = (unsigned)(ctx->n_tiles + (a.n + kTileChunk - 1) / kTileChunk);
   switch (ctx->shape_order) {
-    case 1: push32_tile_kernel<1><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
-    case 2: push32_tile_kernel<2><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
-    default: push32_tile_kernel<3><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+    case 1: push32_tile_kernel<1, false><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+    case 2: push32_tile_kernel<2, false><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+    default: push32_tile_kernel<3, false><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
   }
   PIC_LAUNCH_CHECK(ctx);
+  // the twin only on a grid moving along z (v_gal_z != 0), where a plasma at rest streams through
+  // the grid; elsewhere a species with a z frame velocity takes the per-particle J blocks of the
+  // first launch
+  if (a.frame != nullptr && a.vg[2] != 0.0f) {
+    switch (ctx->shape_order) {
+      case 1: push32_tile_kernel<1, true><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+      case 2: push32_tile_kernel<2, true><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+      default: push32_tile_kernel<3, true><<<nb, kTileThreads, smem, ctx->stream>>>(a, t); break;
+    }
+    PIC_LAUNCH_CHECK(ctx);
+  }
   return PIC_OK;
 }
 

@@ -45,11 +45,11 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 # ncu capture of the current kernel version: at the full laser-wakefield size, and for the
 # beam-driven box on a 128 x 128 x 512 box of the same physics scaled by 8 (particles and cells);
 # other workloads / forms report null
-MEASURED_TRAFFIC = {("beam_wakefield", (256, 256, 1024), "fp32"): 7.634e9,
+MEASURED_TRAFFIC = {("beam_wakefield", (256, 256, 1024), "fp32"): 7.611e9,
                     ("laser_wakefield", (128, 128, 512), "fp32"): 1.4945e9}
 # LSU data-pipe wavefronts (shared memory, L1, global) of the push stage per step, same captures:
 # the pipe that bounds the particle kernel on chip issues one wavefront per SM per cycle
-MEASURED_LSU_WAVEFRONTS = {("beam_wakefield", (256, 256, 1024), "fp32"): 2.377e9,
+MEASURED_LSU_WAVEFRONTS = {("beam_wakefield", (256, 256, 1024), "fp32"): 2.073e9,
                            ("laser_wakefield", (128, 128, 512), "fp32"): 4.761e8}
 N_SM = 152
 # CPU-oracle samples: the same workload on a smaller box (same dx, dt, physics)

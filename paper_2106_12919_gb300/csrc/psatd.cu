@@ -435,8 +435,12 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<C> u) {
 // One thread per entry (qx, qy, iz) of the compact tables: the coefficients are read once and
 // applied to the one, two or four modes (+-kx, +-ky, kz) that share them (qx = 0 and Nx / 2 have no
 // mirror along x, likewise along y).  REAL: the standard variant's real tables.
+// register caps: FP32 standard and Galilean variants 64 (4 CTAs per SM, no spills: 0.147 -> 0.128
+// ms on the laser-wakefield box), the averaged variant 128 (at 80 its larger tables spill and it
+// runs slower); FP64 128, and 255 for the averaged variant
 template <int VAR, class C, bool REAL>
-__global__ void __launch_bounds__(256) update_quad_kernel(UpdArgs<C> u) {
+__global__ void __launch_bounds__(256, sizeof(C) == 8 ? (VAR == 2 ? 2 : 4) : (VAR == 2 ? 1 : 2))
+    update_quad_kernel(UpdArgs<C> u) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= u.coef.nq) return;
   const uint32_t nzh = (uint32_t)u.nzh, nqy = (uint32_t)u.coef.nqy;

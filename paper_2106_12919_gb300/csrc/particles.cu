@@ -95,52 +95,77 @@ __device__ __forceinline__ double wrap(double x, double L) {
   return x;
 }
 
+// rho of one particle: node (i, j, k) receives (Sx_i q w)(Sy_j Sz_k); Syz is the caller's storage
 template <int P>
-__global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= a.n) return;
+__device__ __forceinline__ void deposit_rho_nodes(const PushArgs& a, int lx, int ly, int lz, const double* Sx,
+                                                  const double* Sy, const double* Sz, double qw,
+                                                  double (&Syz)[P + 1][P + 1]) {
   constexpr int NS = P + 1;
-  const double x = a.x[p], y = a.y[p], z = a.z[p];
-  const double qw = a.w[p] * a.qw_scale;
-  int lx, ly, lz;
-  double Sx[NS], Sy[NS], Sz[NS];
-  if (!a.gather) {
-    shape<P>(x, a.inv_dx[0], a.mask[0], lx, Sx);
-    shape<P>(y, a.inv_dx[1], a.mask[1], ly, Sy);
-    shape<P>(z, a.inv_dx[2], a.mask[2], lz, Sz);
+  double Sq[NS];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) {
-      const int64_t ox = (int64_t)((lx + i) & a.mask[0]) * a.Ny;
+  for (int i = 0; i < NS; ++i) Sq[i] = Sx[i] * qw;
 #pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        const int64_t oy = (ox + ((ly + j) & a.mask[1])) * a.Nz;
-        const double sxy = Sx[i] * Sy[j] * qw;
+  for (int j = 0; j < NS; ++j)
 #pragma unroll
-        for (int k = 0; k < NS; ++k) atomicAdd(a.rho + oy + ((lz + k) & a.mask[2]), sxy * Sz[k]);
-      }
-    }
-    return;
-  }
-  shape<P>(x, a.inv_dx[0], a.mask[0], lx, Sx);
-  shape<P>(y, a.inv_dx[1], a.mask[1], ly, Sy);
-  shape<P>(z, a.inv_dx[2], a.mask[2], lz, Sz);
-  // gather E, B at x^n
-  double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < NS; ++k) Syz[j][k] = Sy[j] * Sz[k];
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     const int64_t ox = (int64_t)((lx + i) & a.mask[0]) * a.Ny;
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
       const int64_t oy = (ox + ((ly + j) & a.mask[1])) * a.Nz;
-      const double sxy = Sx[i] * Sy[j];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) atomicAdd(a.rho + oy + ((lz + k) & a.mask[2]), Sq[i] * Syz[j][k]);
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void push_particle(const PushArgs& a, int64_t p) {
+  constexpr int NS = P + 1;
+  const double x = a.x[p], y = a.y[p], z = a.z[p];
+  const double qw = a.w[p] * a.qw_scale;
+  int lx, ly, lz;
+  double Sx[NS], Sy[NS], Sz[NS];
+  // The weight of node (i, j, k) is Sx_i Sy_j Sz_k.  Every sum below forms the NS^2 products
+  // Sy_j Sz_k once and carries the particle's factor (q w, or q w v_c) on the NS x weights, so a
+  // node costs one FP64 multiply or FMA per value instead of two (the FP64 pipe bounds this kernel).
+  double Syz[NS][NS];
+  if (!a.gather) {
+    shape<P>(x, a.inv_dx[0], a.mask[0], lx, Sx);
+    shape<P>(y, a.inv_dx[1], a.mask[1], ly, Sy);
+    shape<P>(z, a.inv_dx[2], a.mask[2], lz, Sz);
+    deposit_rho_nodes<P>(a, lx, ly, lz, Sx, Sy, Sz, qw, Syz);
+    return;
+  }
+  shape<P>(x, a.inv_dx[0], a.mask[0], lx, Sx);
+  shape<P>(y, a.inv_dx[1], a.mask[1], ly, Sy);
+  shape<P>(z, a.inv_dx[2], a.mask[2], lz, Sz);
+  // gather E, B at x^n: f_c = sum_i Sx_i g_ic, g_ic = sum_jk (Sy_j Sz_k) F_c(i, j, k)
+#pragma unroll
+  for (int j = 0; j < NS; ++j)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Syz[j][k] = Sy[j] * Sz[k];
+  double f[6];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const int64_t ox = (int64_t)((lx + i) & a.mask[0]) * a.Ny;
+    double g[6];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const int64_t oy = (ox + ((ly + j) & a.mask[1])) * a.Nz;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         const int64_t o = oy + ((lz + k) & a.mask[2]);
-        const double s = sxy * Sz[k];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) f[c] += s * __ldg(a.F[c] + o);
+        for (int c = 0; c < 6; ++c) {
+          const double v = __ldg(a.F[c] + o);
+          g[c] = (j == 0 && k == 0) ? Syz[j][k] * v : fma(Syz[j][k], v, g[c]);
+        }
       }
     }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) f[c] = i == 0 ? Sx[0] * g[c] : fma(Sx[i], g[c], f[c]);
   }
   // push u^{n-1/2} -> u^{n+1/2}
   double ux, uy, uz;
@@ -162,20 +187,29 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
   shape<P>(my, a.inv_dx[1], a.mask[1], ly, Sy);
   shape<P>(mz, a.inv_dx[2], a.mask[2], lz, Sz);
   const double jx = qw * vx, jy = qw * vy, jz = qw * vz;
+  double Sj[3][NS];  // (Sx_i q w v_c)
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    Sj[0][i] = Sx[i] * jx;
+    Sj[1][i] = Sx[i] * jy;
+    Sj[2][i] = Sx[i] * jz;
+  }
+#pragma unroll
+  for (int j = 0; j < NS; ++j)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Syz[j][k] = Sy[j] * Sz[k];
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     const int64_t ox = (int64_t)((lx + i) & a.mask[0]) * a.Ny;
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
       const int64_t oy = (ox + ((ly + j) & a.mask[1])) * a.Nz;
-      const double sxy = Sx[i] * Sy[j];
 #pragma unroll
       for (int kk = 0; kk < NS; ++kk) {
         const int64_t o = oy + ((lz + kk) & a.mask[2]);
-        const double s = sxy * Sz[kk];
-        atomicAdd(a.J[0] + o, s * jx);
-        atomicAdd(a.J[1] + o, s * jy);
-        atomicAdd(a.J[2] + o, s * jz);
+        atomicAdd(a.J[0] + o, Sj[0][i] * Syz[j][kk]);
+        atomicAdd(a.J[1] + o, Sj[1][i] * Syz[j][kk]);
+        atomicAdd(a.J[2] + o, Sj[2][i] * Syz[j][kk]);
       }
     }
   }
@@ -183,17 +217,20 @@ __global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
   shape<P>(nx, a.inv_dx[0], a.mask[0], lx, Sx);
   shape<P>(ny, a.inv_dx[1], a.mask[1], ly, Sy);
   shape<P>(nz, a.inv_dx[2], a.mask[2], lz, Sz);
-#pragma unroll
-  for (int i = 0; i < NS; ++i) {
-    const int64_t ox = (int64_t)((lx + i) & a.mask[0]) * a.Ny;
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      const int64_t oy = (ox + ((ly + j) & a.mask[1])) * a.Nz;
-      const double sxy = Sx[i] * Sy[j] * qw;
-#pragma unroll
-      for (int kk = 0; kk < NS; ++kk) atomicAdd(a.rho + oy + ((lz + kk) & a.mask[2]), sxy * Sz[kk]);
-    }
-  }
+  deposit_rho_nodes<P>(a, lx, ly, lz, Sx, Sy, Sz, qw, Syz);
+}
+
+// The cubic form holds 128 registers (2 CTAs of 256 threads per SM, no spills); orders 1 and 2 keep
+// the compiler's own choice (64 and ~100 registers).
+template <int P>
+__global__ void __launch_bounds__(256) push_kernel(PushArgs a) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < a.n) push_particle<P>(a, p);
+}
+template <>
+__global__ void __launch_bounds__(256, 2) push_kernel<3>(PushArgs a) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < a.n) push_particle<3>(a, p);
 }
 
 // Staggered comparison cycle (Sec. 2): E, B are gathered from their own Yee positions and J is

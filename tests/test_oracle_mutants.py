@@ -196,3 +196,27 @@ def test_update_transpose_without_the_conjugate(monkeypatch):
     monkeypatch.setattr(adjoint, "update_T", lambda Eb, Bb, co, k, c=1.0:
                         orig(Eb, Bb, {key: np.conj(v) for key, v in co.items()}, k, c))
     _fails(T_adj.test_maxwell_transpose_dot_product, 1, (0, 0, 0.8), (8, 8, 8))
+
+
+def test_fields_gathered_without_centering(monkeypatch):
+    # Yee E, B read as if they were nodal: a half-cell staggering error the mirror symmetry exposes
+    import test_oracle_symmetry as T_sym
+    monkeypatch.setattr(grid, "center_to_nodal", lambda f, name, orders: np.asarray(f))
+    _fails(T_sym.test_mirror_reflection_x, 0, 0.0, 2, 0)
+
+
+def test_current_solved_without_centering(monkeypatch):
+    import test_oracle_symmetry as T_sym
+    monkeypatch.setattr(grid, "center_to_yee", lambda f, name, orders: np.asarray(f))
+    _fails(T_sym.test_mirror_reflection_x, 0, 0.0, 2, 0)
+
+
+def test_curl_with_one_component_sign_flipped(monkeypatch):
+    import test_oracle_step as T_step
+    orig = psatd.cross
+
+    def wrong(k, F):
+        r = orig(k, F)
+        return [r[0], -r[1], r[2]]
+    monkeypatch.setattr(psatd, "cross", wrong)
+    _fails(T_step.test_vacuum_energy_conserved, 0, (0, 0, 0), 0.0)
